@@ -1,0 +1,268 @@
+/*
+ * cheb.h -- C ABI of libcheb.so: sparse Chebyshev matrix functions on one GB300.
+ *
+ * The library evaluates f(M) ~ p(M) = c_0/2 I + sum_{k>=1} c_k T_k(M~) (Eq. 1)
+ * for a 4x4-block-sparse symmetric M, with the spectrum mapped into [-1, 1]
+ * (Eq. 2), the Chebyshev matrices from the three-term recursion (Eq. 3), each
+ * product truncated to a fixed output sparsity pattern with buffer regions
+ * (Sec. "Sparsity and truncation"), and the coefficients from Eq. 4 with the
+ * degree picked by Eq. 6.  On top of it: Fermi-operator expansion with the
+ * S^-1/2 transformation and the mu search on Tr(KS) = N (Sec. "Fermi Operator
+ * Expansion"), matrix powers (Sec. "Matrix powers"), selected eigenvalues
+ * (Sec. "Extraction of selected eigenvalues") and bound checks (Eq. 5).
+ *
+ * Conventions (all calls):
+ *  - Every function returns int: CHEB_OK or one of the CHEB_ERR_* codes; the
+ *    message of the last failure in the calling thread is cheb_last_error().
+ *  - Matrices are block-CSR with 4x4 row-major blocks (cheb_bsr).  row_ptr is
+ *    int64[nbr+1], col_idx int32[nnzb] sorted ascending within each row, vals
+ *    nnzb*16 elements.  Unless stated otherwise every pointer is DEVICE memory
+ *    owned by the caller; the library never frees it.
+ *  - The library allocates no device memory.  Scratch memory comes from the
+ *    caller through a workspace argument; each call documents how to size it.
+ *    Host memory is allocated only for plan objects (cheb_plan_create).
+ *  - Every call takes a cudaStream_t (passed as void*, NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream unless documented as
+ *    "host-returning", in which case they synchronise the stream before they
+ *    return their host outputs.
+ *  - Output patterns must be symmetric and contain every diagonal block.
+ */
+#ifndef CHEB_H
+#define CHEB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    CHEB_OK = 0,
+    CHEB_ERR_INVALID = 1,       /* bad argument, size or pattern */
+    CHEB_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+    CHEB_ERR_NOT_SPD = 3,       /* lower spectral bound <= 0 where a positive one is required */
+    CHEB_ERR_BOUNDS = 4,        /* penalty check (Eq. 5) says the bounds do not hold */
+    CHEB_ERR_NOT_CONVERGED = 5, /* iteration cap reached (mu bisection, degree search) */
+    CHEB_ERR_TIMEOUT = 6,       /* a device-side wait gave up after its time limit */
+    CHEB_ERR_NOSPACE = 7        /* workspace too small, or a pattern too wide for the kernels */
+};
+
+/* Element types of matrix values. */
+enum { CHEB_F64 = 0, CHEB_F32 = 1, CHEB_BF16 = 2 };
+
+/* Function kinds for cheb_func.kind (all in the unscaled variable x). */
+enum {
+    CHEB_FERMI = 0,    /* 1/(1+exp((x-mu)/kT)), Eq. 7 with beta = 1/kT */
+    CHEB_ERFC = 1,     /* 0.5*erfc((x-mu)/kT), Eq. 9 with beta = 1/kT */
+    CHEB_POWER = 2,    /* x^a, Sec. "Matrix powers" (x > 0 on the interval) */
+    CHEB_INTERVAL = 3, /* Fermi(x; mu=hi) - Fermi(x; mu=lo): states in [lo, hi] */
+    CHEB_PENALTY = 4   /* Eq. 5 in the scaled variable xs in [-1,1]:
+                          exp(-|a|(xs+1)) - exp(|a|(xs-1)) */
+};
+
+typedef struct cheb_bsr {
+    int64_t nbr;            /* block rows (= block columns) */
+    int64_t nnzb;           /* stored 4x4 blocks */
+    const int64_t *row_ptr; /* device, int64[nbr+1] */
+    const int32_t *col_idx; /* device, int32[nnzb], ascending within each row */
+    void *vals;             /* device, nnzb*16 elements of type dtype (may be NULL for a pattern) */
+    int32_t dtype;          /* CHEB_F64 / CHEB_F32 / CHEB_BF16 */
+} cheb_bsr;
+
+typedef struct cheb_func {
+    int32_t kind; /* CHEB_FERMI ... */
+    double mu;    /* chemical potential (FERMI, ERFC) */
+    double kT;    /* smearing width (FERMI, ERFC, INTERVAL) */
+    double a;     /* exponent (POWER) or alpha (PENALTY) */
+    double lo;    /* interval ends (INTERVAL) */
+    double hi;
+} cheb_func;
+
+/* Message of the last failure in this thread ("" if none).  Never NULL. */
+const char *cheb_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Sparsity patterns.  Sec. "Sparsity and truncation": the library works on a
+ * fixed pattern; the output pattern is a larger "buffer" pattern.  Both are
+ * built here from atom positions by a distance cutoff, as in the paper's tests
+ * (Sec. "Performance").
+ *
+ * cheb_pattern_build: block pattern {(I,J) : minimum-image distance <= r_cut}
+ * (inclusive, diagonal always present) for n_atoms atoms in a periodic cube
+ * of edge box_L.  xyz: device double[n_atoms][3], coordinates in [0, box_L).
+ * The distance test is done in float64 without fused multiply-add:
+ * dx = x_J - x_I wrapped once by +-box_L when |dx| > box_L/2, then
+ * (dx*dx + dy*dy) + dz*dz <= r_cut*r_cut.
+ * Two calls: with col_idx == NULL it writes row_ptr (device int64[n_atoms+1])
+ * and returns the block count in *nnzb (host-returning); with col_idx != NULL
+ * (device int32[*nnzb]) and the row_ptr of the first call it fills the sorted
+ * column lists (asynchronous).  Errors: CHEB_ERR_INVALID for n_atoms < 1,
+ * box_L <= 0 or r_cut < 0.
+ */
+int cheb_pattern_build(const double *xyz, int64_t n_atoms, double box_L, double r_cut,
+                       int64_t *row_ptr, int32_t *col_idx, int64_t *nnzb, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Plans.  A plan holds what the masked products need to know about the output
+ * pattern P_out (symmetric): the transposition map of its blocks and the
+ * grouping of its block columns into panels that one thread block advances
+ * together (columns are independent under Eq. 3, Sec. "Expansion in Chebyshev
+ * polynomials").  precision (CHEB_F64 / CHEB_F32) selects the panel width.
+ *
+ * cheb_plan_create (host-returning): reads P_out's row_ptr/col_idx (device)
+ * to the host, checks symmetry, sortedness and diagonal blocks
+ * (CHEB_ERR_INVALID otherwise), groups columns, and returns a host-allocated
+ * plan and the device workspace it needs in *plan_ws_bytes.
+ * cheb_plan_bind copies the plan tables into caller device memory plan_ws
+ * (>= plan_ws_bytes, 256-byte aligned); the plan then refers to that memory,
+ * which must stay valid until cheb_plan_destroy.  P_out's row_ptr/col_idx
+ * pointers are remembered by the plan and must stay valid too.
+ * cheb_plan_info reports (n_panels, panel width, max panel union rows).
+ */
+typedef struct cheb_plan cheb_plan;
+
+int cheb_plan_create(const cheb_bsr *P_out, int32_t precision, cheb_plan **plan,
+                     size_t *plan_ws_bytes, void *stream);
+int cheb_plan_bind(cheb_plan *plan, void *plan_ws, size_t plan_ws_bytes, void *stream);
+int cheb_plan_info(const cheb_plan *plan, int64_t *n_panels, int32_t *panel_width,
+                   int32_t *max_union);
+int cheb_plan_destroy(cheb_plan *plan);
+
+/* ---------------------------------------------------------------------------
+ * Eq. 2: M~ = sigma (M - tau I), sigma = 2/(emax-emin), tau = (emin+emax)/2.
+ * M: FP64 matrix with every diagonal block present; out: device double[nnzb*16]
+ * on M's pattern (may alias M->vals).  Asynchronous.
+ */
+int cheb_scale(const cheb_bsr *M, double emin, double emax, double *out, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Spectral bounds (Sec. "Determination of the eigenvalue bounds ..."): k steps
+ * of plain Lanczos on the FP64 matrix M from start vector v0 (device
+ * double[4*nbr]; NULL means the all-ones vector), then the extreme eigenvalues
+ * theta_min/max of the Lanczos tridiagonal and the residuals
+ * beta_k |s| of their Ritz pairs.  *emin = theta_min - m_lo, *emax = theta_max
+ * + m_hi with m = max(2*residual, margin_frac*(theta_max - theta_min)).
+ * Host-returning.  theta (host double[2], may be NULL) receives theta_min/max.
+ * Workspace: cheb_bounds_workspace_size.  Errors: CHEB_ERR_INVALID for k < 1
+ * or k > 512.
+ */
+int cheb_bounds_workspace_size(int64_t nbr, int32_t k, size_t *bytes);
+int cheb_bounds(const cheb_bsr *M, int32_t k, const double *v0, double margin_frac,
+                double *emin, double *emax, double *theta, void *ws, size_t ws_bytes,
+                void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Coefficients (Eq. 4) and degree (Eq. 6).  For each of the n_f functions
+ * (host array funcs) on the interval [emin, emax]:
+ *   c_j = (2/n) sum_{k<n} f(cos(pi(k+1/2)/n)/sigma + tau) cos(pi j (k+1/2)/n).
+ * If tol > 0 the term count n is the smallest entry of the ladder
+ * {m * 2^e : 8 <= m <= 15, e >= 1} in [16, n_max] whose maximum fit error
+ * |p_n - f| over 8193 uniform points plus the 2n+1 extrema of T_{2n} is below
+ * tol (divided by max|f| when rel != 0), taken as the largest such n over the
+ * n_f functions; if tol <= 0, n = n_max.  coeffs: device double[n_f][n_max],
+ * entries j >= n set to 0.  *n_out (host) receives n.  Host-returning.
+ * Errors: CHEB_ERR_NOT_CONVERGED if no ladder entry <= n_max reaches tol;
+ * CHEB_ERR_INVALID for n_f < 1, n_max < 16, emax <= emin.
+ */
+int cheb_coeffs_workspace_size(int32_t n_f, int32_t n_max, size_t *bytes);
+int cheb_coeffs(const cheb_func *funcs, int32_t n_f, double emin, double emax, double tol,
+                int32_t rel, int32_t n_max, int32_t *n_out, double *coeffs, void *ws,
+                size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * The fused recursion (Eq. 1 + Eq. 3).  Mt: the scaled operator (FP64, pattern
+ * P_L with every diagonal block, P_L contained in the plan's P_out, nbr equal).
+ * For k = 0..n_terms-1 it forms T_0 = I, T_1 = Mt, T_{k+1} = 2 P_out(Mt T_k)
+ * - T_{k-1} (left multiplication, no symmetrisation) and, fused into the same
+ * pass, acc_j += coeffs[j][k] T_k for every j < n_f (c_0 halved, Eq. 1),
+ * moments[k] = Tr T_k and gmoments[k] = <T_k, G> (sum over P_out of
+ * elementwise products) when G is given.
+ *   coeffs: device double[n_f][coeff_stride]; acc: host array of n_f device
+ *   pointers, each double[nnzb(P_out)*16] in BCSR order on P_out (overwritten);
+ *   moments, gmoments: device double[n_terms] or NULL; G: device double on
+ *   P_out or NULL.  precision: CHEB_F64 (T_k and products in FP64) or CHEB_F32
+ *   (Mt rounded to FP32, T_k stored and multiplied in FP32, accumulators and
+ *   moments in FP64).  Asynchronous.  Workspace: cheb_expand_workspace_size.
+ * Errors: CHEB_ERR_INVALID (n_terms < 2, n_f < 0 or > 8, plan precision !=
+ * precision), CHEB_ERR_NOSPACE (workspace too small).
+ */
+int cheb_expand_workspace_size(const cheb_plan *plan, const cheb_bsr *Mt, int32_t precision,
+                               size_t *bytes);
+int cheb_expand(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_terms,
+                const double *coeffs, int32_t coeff_stride, int32_t n_f, double *const *acc,
+                double *moments, const double *G, double *gmoments, int32_t precision,
+                void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * One masked product (the building block of Eq. 3 outside the recursion):
+ *   C = alpha P_out(L R) + beta D
+ * L: FP64 BCSR with nbr rows (any pattern); R, D, C: FP64 values on the plan's
+ * P_out (BCSR order).  D may be NULL (beta ignored).  C must not alias R or D.
+ * The plan must be an FP64 plan.  Asynchronous; no workspace.
+ */
+int cheb_masked_product(const cheb_plan *plan, const cheb_bsr *L, const double *R, double alpha,
+                        const double *D, double beta, double *C, void *stream);
+
+/* Block transpose on the plan's symmetric pattern: out = A^T.  FP64; out must
+ * not alias A.  Asynchronous. */
+int cheb_transpose(const cheb_plan *plan, const double *A, double *out, void *stream);
+
+/* Keep the blocks of A (FP64 on pattern PA) that lie in pattern P (contained
+ * in PA): out = device double[P->nnzb*16].  Asynchronous. */
+int cheb_restrict(const cheb_bsr *A, const cheb_bsr *P, double *out, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Trace (Sec. "Fermi Operator Expansion": Tr(KS) = N).  out (device double[1])
+ * = sum over the blocks (i,j) of B's pattern of A_ij * B_ij, which is Tr(A B)
+ * for symmetric B.  B's pattern must be contained in A's.  FP64.
+ * Asynchronous.  Workspace: cheb_trace_workspace_size.
+ */
+int cheb_trace_workspace_size(const cheb_bsr *B, size_t *bytes);
+int cheb_trace(const cheb_bsr *A, const cheb_bsr *B, double *out, void *ws, size_t ws_bytes,
+               void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Penalty check, Eq. 5: out (device double[1]) = c^p_0/2 t_0 + sum_k c^p_k t_k
+ * with c^p from Eq. 4 for CHEB_PENALTY with parameter alpha, n_terms = length
+ * of the moment vector t (device).  The bounds hold when |out| is below a
+ * threshold chosen by the caller.  Asynchronous.  Workspace: 8*n_terms bytes.
+ */
+int cheb_penalty_trace(const double *moments, int32_t n_terms, double alpha, double *out,
+                       void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * mu search (Sec. "Fermi Operator Expansion": adjust mu until Tr(KS) = N, by
+ * re-summing the expansion with new coefficients).  gmoments: device
+ * double[n_terms], g_k = Tr(post(T_k) S).  N(mu) = c_0(mu) g_0/2 +
+ * sum_k c_k(mu) g_k with c(mu) from Eq. 4 for kind (CHEB_FERMI or CHEB_ERFC)
+ * and width kT on [emin, emax].  Bisection on the bracket (lo, hi) (host
+ * double[2]; NULL = [emin, emax]): mid = (lo+hi)/2 in float64, decision bit =
+ * [N(mid) > N_e] (then hi = mid, else lo = mid), stop when |N(mid) - N_e| <=
+ * tol_N or after max_iter (<= 128) iterations.
+ * result: device buffer of 4 doubles + 2 uint64 = 48 bytes:
+ *   [0] mu, [1] N(mu), [2] iterations, [3] 1.0 if converged else 0.0,
+ *   then bits[2] (bit i of the 128-bit word = decision of iteration i).
+ * Asynchronous.  Workspace: 8*n_terms bytes.
+ */
+int cheb_mu_search(const double *gmoments, int32_t n_terms, double emin, double emax,
+                   int32_t kind, double kT, double N_e, double tol_N, int32_t max_iter,
+                   const double *bracket, void *result, void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * One FP64 in-pattern Newton-Schulz step for S^-1 (not in the paper; repairs
+ * the precision of a reduced-precision expansion):
+ *   X1 = 2 X0 - P_out(X0 P_out(S X0)).
+ * S: FP64 on P_S (contained in P_out); X0, X1: FP64 on the plan's P_out; tmp:
+ * device double[nnzb(P_out)*16] scratch.  X1 must not alias X0 or tmp.
+ * Asynchronous.
+ */
+int cheb_newton_schulz(const cheb_plan *plan, const cheb_bsr *S, const double *X0, double *X1,
+                       double *tmp, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEB_H */

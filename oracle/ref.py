@@ -311,16 +311,20 @@ def cheb_coeffs(f: Func, n: int, emin: float, emax: float) -> np.ndarray:
 
     i.e. f sampled at the n Chebyshev nodes mapped back to the unscaled interval
     (Eq. 2).  The expansion uses these n coefficients with c_0 halved (Eq. 1).
+    The cosine argument pi j (2k+1)/(2n) is reduced exactly (integer j(2k+1)
+    modulo 4n) before the cosine, so large j k lose no precision.
     """
     s, t = sigma_tau(emin, emax)
     k = np.arange(n, dtype=np.float64)
     xk = np.cos(np.pi * (k + 0.5) / n)
     fk = f(xk / s + t, emin, emax)
     c = np.empty(n)
+    k2 = 2 * np.arange(n, dtype=np.int64) + 1
     step = max(1, 4_000_000 // max(n, 1))
     for j0 in range(0, n, step):
-        j = np.arange(j0, min(n, j0 + step), dtype=np.float64)
-        c[j0:j0 + len(j)] = (2.0 / n) * (np.cos(np.pi * np.outer(j, k + 0.5) / n) @ fk)
+        j = np.arange(j0, min(n, j0 + step), dtype=np.int64)
+        idx = np.outer(j, k2) % (4 * n)
+        c[j0:j0 + len(j)] = (2.0 / n) * (np.cos(np.pi * idx / (2 * n)) @ fk)
     return c
 
 

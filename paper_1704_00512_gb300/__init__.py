@@ -1,0 +1,11 @@
+"""GB300-native sparse Chebyshev matrix functions (the CheSS method, arXiv:1704.00512).
+
+The computation lives in libcheb.so (CUDA, sm_103a) behind the C ABI of
+include/cheb.h.  This package is its thin Python binding (``_lib``, same names as
+the C entry points) plus the solve sequences (``solve``) that chain those calls.
+"""
+from ._lib import (  # noqa: F401
+    BF16, ERFC, F32, F64, FERMI, INTERVAL, PENALTY, POWER, Bsr, ChebError, Plan, bounds, coeffs,
+    decode_mu_result, expand, expand_workspace_size, load, masked_product, mu_search, newton_schulz,
+    pattern_build, penalty_trace, restrict, scale, trace, transpose,
+)

@@ -1,0 +1,336 @@
+"""ctypes binding of libcheb.so: argument marshalling only.
+
+Every function here has the name of the C entry point it calls (without the
+``cheb_`` prefix), takes torch CUDA tensors for device memory, allocates the
+workspace the call asks for with torch, and raises ``ChebError`` on a non-zero
+status.  No computation happens in Python: a missing or unloadable library is
+an error, never a fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcheb.so")
+
+OK, ERR_INVALID, ERR_CUDA, ERR_NOT_SPD, ERR_BOUNDS, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_NOSPACE = range(8)
+F64, F32, BF16 = 0, 1, 2
+FERMI, ERFC, POWER, INTERVAL, PENALTY = 0, 1, 2, 3, 4
+
+# Every symbol declared in include/cheb.h.
+EXPORTS = [
+    "cheb_last_error", "cheb_pattern_build", "cheb_plan_create", "cheb_plan_bind", "cheb_plan_info",
+    "cheb_plan_destroy", "cheb_scale", "cheb_bounds_workspace_size", "cheb_bounds",
+    "cheb_coeffs_workspace_size", "cheb_coeffs", "cheb_expand_workspace_size", "cheb_expand",
+    "cheb_masked_product", "cheb_transpose", "cheb_restrict", "cheb_trace_workspace_size", "cheb_trace",
+    "cheb_penalty_trace", "cheb_mu_search", "cheb_newton_schulz",
+]
+
+
+class ChebError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libcheb error {code}: {msg}")
+        self.code = code
+
+
+class CBsr(ctypes.Structure):
+    _fields_ = [("nbr", ctypes.c_int64), ("nnzb", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("dtype", ctypes.c_int32)]
+
+
+class CFunc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("mu", ctypes.c_double), ("kT", ctypes.c_double),
+                ("a", ctypes.c_double), ("lo", ctypes.c_double), ("hi", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libcheb.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise ChebError(ERR_INVALID, f"libcheb.so not found at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    p, i32, i64, dbl, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+    P = ctypes.POINTER
+    sig = {
+        "cheb_last_error": ([], ctypes.c_char_p),
+        "cheb_pattern_build": ([p, i64, dbl, dbl, p, p, P(i64), p], i32),
+        "cheb_plan_create": ([P(CBsr), i32, P(p), P(sz), p], i32),
+        "cheb_plan_bind": ([p, p, sz, p], i32),
+        "cheb_plan_info": ([p, P(i64), P(i32), P(i32)], i32),
+        "cheb_plan_destroy": ([p], i32),
+        "cheb_scale": ([P(CBsr), dbl, dbl, p, p], i32),
+        "cheb_bounds_workspace_size": ([i64, i32, P(sz)], i32),
+        "cheb_bounds": ([P(CBsr), i32, p, dbl, P(dbl), P(dbl), P(dbl), p, sz, p], i32),
+        "cheb_coeffs_workspace_size": ([i32, i32, P(sz)], i32),
+        "cheb_coeffs": ([P(CFunc), i32, dbl, dbl, dbl, i32, i32, P(i32), p, p, sz, p], i32),
+        "cheb_expand_workspace_size": ([p, P(CBsr), i32, P(sz)], i32),
+        "cheb_expand": ([p, P(CBsr), i32, p, i32, i32, P(p), p, p, p, i32, p, sz, p], i32),
+        "cheb_masked_product": ([p, P(CBsr), p, dbl, p, dbl, p, p], i32),
+        "cheb_transpose": ([p, p, p, p], i32),
+        "cheb_restrict": ([P(CBsr), P(CBsr), p, p], i32),
+        "cheb_trace_workspace_size": ([P(CBsr), P(sz)], i32),
+        "cheb_trace": ([P(CBsr), P(CBsr), p, p, sz, p], i32),
+        "cheb_penalty_trace": ([p, i32, dbl, p, p, sz, p], i32),
+        "cheb_mu_search": ([p, i32, dbl, dbl, i32, dbl, dbl, dbl, i32, p, p, p, sz, p], i32),
+        "cheb_newton_schulz": ([p, P(CBsr), p, p, p, p], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        msg = _lib.cheb_last_error().decode()
+        raise ChebError(rc, msg)
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _ws(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256) + 256, dtype=torch.uint8, device=device)
+
+
+def _aligned(t: torch.Tensor) -> int:
+    p = t.data_ptr()
+    return (p + 255) // 256 * 256
+
+
+class Bsr:
+    """4x4 block-CSR matrix on the GPU: row_ptr int64, col_idx int32, vals [nnzb, 4, 4]."""
+
+    def __init__(self, row_ptr: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tensor | None = None):
+        self.row_ptr = row_ptr
+        self.col_idx = col_idx
+        self.vals = vals
+
+    @property
+    def nbr(self) -> int:
+        return self.row_ptr.numel() - 1
+
+    @property
+    def nnzb(self) -> int:
+        return self.col_idx.numel()
+
+    def with_vals(self, vals: torch.Tensor) -> "Bsr":
+        return Bsr(self.row_ptr, self.col_idx, vals)
+
+    def c(self) -> CBsr:
+        dt = F64
+        if self.vals is not None:
+            dt = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}[self.vals.dtype]
+        return CBsr(self.nbr, self.nnzb, _ptr(self.row_ptr), _ptr(self.col_idx),
+                    _ptr(self.vals) if self.vals is not None else None, dt)
+
+
+def pattern_build(xyz: torch.Tensor, box_L: float, r_cut: float, stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+    """cheb_pattern_build (both calls)."""
+    lib = load()
+    n = xyz.shape[0]
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=xyz.device)
+    nnzb = ctypes.c_int64(0)
+    s = _stream(stream)
+    _check(lib.cheb_pattern_build(_ptr(xyz), n, box_L, r_cut, _ptr(row_ptr), None, ctypes.byref(nnzb), s))
+    col_idx = torch.empty(nnzb.value, dtype=torch.int32, device=xyz.device)
+    _check(lib.cheb_pattern_build(_ptr(xyz), n, box_L, r_cut, _ptr(row_ptr), _ptr(col_idx), None, s))
+    return row_ptr, col_idx
+
+
+class Plan:
+    """cheb_plan_create + cheb_plan_bind; keeps the pattern and workspace alive."""
+
+    def __init__(self, P_out: Bsr, precision: int = F64, stream=None):
+        lib = load()
+        self.P_out = P_out
+        self.precision = precision
+        h = ctypes.c_void_p()
+        nbytes = ctypes.c_size_t(0)
+        s = _stream(stream)
+        cb = P_out.c()
+        _check(lib.cheb_plan_create(ctypes.byref(cb), precision, ctypes.byref(h), ctypes.byref(nbytes), s))
+        self.handle = h
+        self._ws = _ws(nbytes.value, P_out.row_ptr.device)
+        _check(lib.cheb_plan_bind(h, ctypes.c_void_p(_aligned(self._ws)), nbytes.value, s))
+
+    def info(self) -> tuple[int, int, int]:
+        a, b, c = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.cheb_plan_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.cheb_plan_destroy(self.handle)
+            self.handle = None
+
+
+def scale(M: Bsr, emin: float, emax: float, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    lib = load()
+    out = torch.empty_like(M.vals) if out is None else out
+    cb = M.c()
+    _check(lib.cheb_scale(ctypes.byref(cb), emin, emax, _ptr(out), _stream(stream)))
+    return out
+
+
+def bounds(M: Bsr, k: int = 40, v0: torch.Tensor | None = None, margin_frac: float = 0.01,
+           stream=None) -> tuple[float, float, tuple[float, float]]:
+    """cheb_bounds: returns (emin, emax, (theta_min, theta_max))."""
+    lib = load()
+    nb = ctypes.c_size_t(0)
+    _check(lib.cheb_bounds_workspace_size(M.nbr, k, ctypes.byref(nb)))
+    ws = _ws(nb.value, M.vals.device)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    th = (ctypes.c_double * 2)()
+    cb = M.c()
+    _check(lib.cheb_bounds(ctypes.byref(cb), k, _ptr(v0), margin_frac, ctypes.byref(lo), ctypes.byref(hi), th,
+                           ctypes.c_void_p(_aligned(ws)), nb.value, _stream(stream)))
+    return lo.value, hi.value, (th[0], th[1])
+
+
+def make_funcs(funcs) -> ctypes.Array:
+    arr = (CFunc * len(funcs))()
+    for i, f in enumerate(funcs):
+        arr[i] = CFunc(int(f["kind"]), float(f.get("mu", 0.0)), float(f.get("kT", 0.0)), float(f.get("a", 0.0)),
+                       float(f.get("lo", 0.0)), float(f.get("hi", 0.0)))
+    return arr
+
+
+def coeffs(funcs, emin: float, emax: float, tol: float, n_max: int, rel: bool = False, device="cuda",
+           stream=None) -> tuple[int, torch.Tensor]:
+    """cheb_coeffs: returns (n, device tensor [n_f, n_max] with zeros beyond n)."""
+    lib = load()
+    nf = len(funcs)
+    nb = ctypes.c_size_t(0)
+    _check(lib.cheb_coeffs_workspace_size(nf, n_max, ctypes.byref(nb)))
+    ws = _ws(nb.value, device)
+    out = torch.empty((nf, n_max), dtype=torch.float64, device=device)
+    n = ctypes.c_int32(0)
+    _check(lib.cheb_coeffs(make_funcs(funcs), nf, emin, emax, tol, int(rel), n_max, ctypes.byref(n), _ptr(out),
+                           ctypes.c_void_p(_aligned(ws)), nb.value, _stream(stream)))
+    return n.value, out
+
+
+def expand_workspace_size(plan: Plan, Mt: Bsr, precision: int) -> int:
+    nb = ctypes.c_size_t(0)
+    cb = Mt.c()
+    _check(load().cheb_expand_workspace_size(plan.handle, ctypes.byref(cb), precision, ctypes.byref(nb)))
+    return nb.value
+
+
+def expand(plan: Plan, Mt: Bsr, n_terms: int, coeffs: torch.Tensor | None, acc: list[torch.Tensor],
+           moments: torch.Tensor | None = None, G: torch.Tensor | None = None, gmoments: torch.Tensor | None = None,
+           precision: int = F64, ws: torch.Tensor | None = None, stream=None):
+    """cheb_expand.  acc: list of FP64 tensors on P_out (overwritten)."""
+    lib = load()
+    need = expand_workspace_size(plan, Mt, precision)
+    if ws is None or ws.numel() < need + 256:
+        ws = _ws(need, Mt.vals.device)
+    nf = len(acc)
+    arr = (ctypes.c_void_p * max(nf, 1))(*[t.data_ptr() for t in acc])
+    stride = coeffs.shape[1] if coeffs is not None else n_terms
+    cb = Mt.c()
+    _check(lib.cheb_expand(plan.handle, ctypes.byref(cb), n_terms, _ptr(coeffs), stride, nf, arr, _ptr(moments),
+                           _ptr(G), _ptr(gmoments), precision, ctypes.c_void_p(_aligned(ws)), need,
+                           _stream(stream)))
+    return ws
+
+
+def masked_product(plan: Plan, L: Bsr, R: torch.Tensor, C: torch.Tensor, alpha: float = 1.0,
+                   D: torch.Tensor | None = None, beta: float = 0.0, stream=None) -> torch.Tensor:
+    cb = L.c()
+    _check(load().cheb_masked_product(plan.handle, ctypes.byref(cb), _ptr(R), alpha, _ptr(D), beta, _ptr(C),
+                                      _stream(stream)))
+    return C
+
+
+def transpose(plan: Plan, A: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    out = torch.empty_like(A) if out is None else out
+    _check(load().cheb_transpose(plan.handle, _ptr(A), _ptr(out), _stream(stream)))
+    return out
+
+
+def restrict(A: Bsr, P: Bsr, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    out = torch.empty((P.nnzb, 4, 4), dtype=torch.float64, device=A.vals.device) if out is None else out
+    ca, cp = A.c(), P.c()
+    _check(load().cheb_restrict(ctypes.byref(ca), ctypes.byref(cp), _ptr(out), _stream(stream)))
+    return out
+
+
+def trace(A: Bsr, B: Bsr, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """cheb_trace: device scalar sum over B's pattern of A_ij B_ij."""
+    lib = load()
+    ca, cbb = A.c(), B.c()
+    nb = ctypes.c_size_t(0)
+    _check(lib.cheb_trace_workspace_size(ctypes.byref(cbb), ctypes.byref(nb)))
+    ws = _ws(nb.value, A.vals.device)
+    out = torch.empty(1, dtype=torch.float64, device=A.vals.device) if out is None else out
+    _check(lib.cheb_trace(ctypes.byref(ca), ctypes.byref(cbb), _ptr(out), ctypes.c_void_p(_aligned(ws)), nb.value,
+                          _stream(stream)))
+    return out
+
+
+def penalty_trace(moments: torch.Tensor, n_terms: int, alpha: float, stream=None) -> torch.Tensor:
+    out = torch.empty(1, dtype=torch.float64, device=moments.device)
+    ws = _ws(8 * n_terms, moments.device)
+    _check(load().cheb_penalty_trace(_ptr(moments), n_terms, alpha, _ptr(out), ctypes.c_void_p(_aligned(ws)),
+                                     8 * n_terms, _stream(stream)))
+    return out
+
+
+def mu_search(gmoments: torch.Tensor, n_terms: int, emin: float, emax: float, kind: int, kT: float, N_e: float,
+              tol_N: float, max_iter: int = 100, bracket: tuple[float, float] | None = None,
+              stream=None) -> torch.Tensor:
+    """cheb_mu_search: returns the 48-byte device result as a uint8 tensor."""
+    res = torch.zeros(48, dtype=torch.uint8, device=gmoments.device)
+    ws = _ws(8 * n_terms, gmoments.device)
+    br = None if bracket is None else (ctypes.c_double * 2)(*bracket)
+    _check(load().cheb_mu_search(_ptr(gmoments), n_terms, emin, emax, kind, kT, N_e, tol_N, max_iter, br,
+                                 _ptr(res), ctypes.c_void_p(_aligned(ws)), 8 * n_terms, _stream(stream)))
+    return res
+
+
+def decode_mu_result(res: torch.Tensor) -> dict:
+    """Unpack the mu-search result (host copy)."""
+    b = res.cpu()
+    d = b[:32].view(torch.float64).tolist()
+    bits = b[32:48].view(torch.int64).tolist()
+    it = int(d[2])
+    word = [x & ((1 << 64) - 1) for x in bits]
+    seq = [(word[i >> 6] >> (i & 63)) & 1 for i in range(it - (1 if d[3] else 0))] if it else []
+    return {"mu": d[0], "N": d[1], "iters": it, "converged": bool(d[3]), "bits": seq}
+
+
+def newton_schulz(plan: Plan, S: Bsr, X0: torch.Tensor, X1: torch.Tensor, tmp: torch.Tensor,
+                  stream=None) -> torch.Tensor:
+    cb = S.c()
+    _check(load().cheb_newton_schulz(plan.handle, ctypes.byref(cb), _ptr(X0), _ptr(X1), _ptr(tmp),
+                                     _stream(stream)))
+    return X1

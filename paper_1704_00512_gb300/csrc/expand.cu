@@ -1,0 +1,522 @@
+// The hot path: one step of the masked Chebyshev recursion (Eq. 3) fused with
+// the accumulation of several expansions (Eq. 1) and the moments that feed the
+// penalty check (Eq. 5) and the mu search.
+//
+// Data flow of one step (one thread block per column panel, see plan.cu):
+//   1. mark the rows of the panel's block columns in a shared bitmap and rank
+//      them (prefix popcounts): the union of the columns' row lists;
+//   2. gather the panel's columns of T_k into shared memory X[slot][4][4P]
+//      (zero where a column has no block in that row);
+//   3. each warp takes union rows I; its 32 lanes split into P column lanes x
+//      32/P K-groups; a lane accumulates the full 4x4 block sum over K of
+//      M~_IK X[K] for its column -- the masked product restricted to the
+//      panel's columns (columns are independent, Sec. "Expansion in Chebyshev
+//      polynomials");
+//   4. K-groups are summed by butterfly shuffles, then the epilogue writes
+//      T_{k+1} = alpha * (M~ T_k) + beta * T_{k-1} for the blocks of P_out only
+//      (the truncation, Sec. "Sparsity and truncation"), adds c_j[k+1] T_{k+1}
+//      to every FP64 accumulator j, and sums Tr T_{k+1} and <T_{k+1}, G>;
+//   5. the last thread block to finish sums the per-block moment partials in
+//      a fixed order (deterministic) and resets the completion counter.
+#include "common.cuh"
+#include "plan.cuh"
+
+namespace cheb {
+
+constexpr int MAX_F = 8;
+
+template <typename T>
+struct StepArgs {
+    int64_t nw;  // bitmap words
+    int32_t ucap;
+    const int64_t *rp;
+    const int32_t *ci;
+    const int32_t *tperm;
+    const int32_t *panels;
+    const int64_t *Lrp;
+    const int32_t *Lci;
+    const T *Lv;
+    const T *R;
+    const T *Rm;
+    T *C;
+    T alpha, beta;
+    int32_t nf;
+    double *acc[MAX_F];
+    const double *coef;
+    int32_t coef_stride;
+    int32_t term;
+    const double *G;
+    double *mom;   // device scalar for Tr T_{k+1} (or NULL)
+    double *gmom;  // device scalar for <T_{k+1}, G> (or NULL)
+    double *part;  // per-block partials
+    int32_t *counter;
+};
+
+template <typename T>
+__device__ __forceinline__ void load16(T (&h)[16], const T *p);
+template <>
+__device__ __forceinline__ void load16<float>(float (&h)[16], const float *p) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float4 v = __ldg(q + i);
+        h[4 * i] = v.x; h[4 * i + 1] = v.y; h[4 * i + 2] = v.z; h[4 * i + 3] = v.w;
+    }
+}
+template <>
+__device__ __forceinline__ void load16<double>(double (&h)[16], const double *p) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        double2 v = __ldg(q + i);
+        h[2 * i] = v.x; h[2 * i + 1] = v.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void lds4(T (&x)[4], const T *p);
+template <>
+__device__ __forceinline__ void lds4<float>(float (&x)[4], const float *p) {
+    float4 v = *reinterpret_cast<const float4 *>(p);
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void lds4<double>(double (&x)[4], const double *p) {
+    double2 a = *reinterpret_cast<const double2 *>(p);
+    double2 b = *reinterpret_cast<const double2 *>(p + 2);
+    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+}
+
+__device__ __forceinline__ int rank_of(const uint2 *bits, int K) {
+    const uint2 w = bits[K >> 5];
+    const unsigned bit = 1u << (K & 31);
+    if (!(w.x & bit)) return -1;
+    return (int)w.y + __popc(w.x & (bit - 1u));
+}
+
+// Exclusive block scan of one int per thread; returns the prefix, *total = sum.
+template <int NW>
+__device__ __forceinline__ int block_excl_scan(int v, int *wsum, int *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int n = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int x = lane < NW ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int n = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += n;
+        }
+        if (lane < NW) wsum[lane] = x;
+    }
+    __syncthreads();
+    const int excl = incl - v + (warp > 0 ? wsum[warp - 1] : 0);
+    *total = wsum[NW - 1];
+    __syncthreads();
+    return excl;
+}
+
+// Deterministic sum of the per-block partials by the last block to finish.
+template <int NT, int NV>
+__device__ __forceinline__ void finish_moments(double *part, int32_t *counter, double (&v)[NV],
+                                               double *const (&dst)[NV], double *red) {
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double w = warp_sum(v[i]);
+        if (lane == 0) red[warp * NV + i] = w;
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < NT / 32; ++w) s += red[w * NV + i];
+            part[(int64_t)blockIdx.x * NV + i] = s;
+        }
+        __threadfence();
+        const int prev = atomicAdd(counter, 1);
+        s_last = prev == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (int b = tid; b < (int)gridDim.x; b += NT) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] += __ldcg(part + (int64_t)b * NV + i);
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double w = warp_sum(acc[i]);
+        if (lane == 0) red[warp * NV + i] = w;
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < NT / 32; ++w) s += red[w * NV + i];
+            if (dst[i]) *dst[i] = s;
+        }
+        *counter = 0;
+        __threadfence();
+    }
+}
+
+template <typename T, int P, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) k_step(const StepArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int wsum[32];
+    __shared__ int s_nu;
+    constexpr int NT = NW * 32;
+    constexpr int KG = 32 / P;                  // K-groups per warp
+    constexpr int EPL = KG >= 16 ? 1 : 16 / KG;  // epilogue elements per lane
+    const StepLayout lay = step_layout(a.nw, a.ucap, P, sizeof(T));
+    uint2 *bits = reinterpret_cast<uint2 *>(smem + lay.off_bits);
+    int32_t *ulist = reinterpret_cast<int32_t *>(smem + lay.off_ulist);
+    int16_t *pos = reinterpret_cast<int16_t *>(smem + lay.off_pos);
+    T *X = reinterpret_cast<T *>(smem + lay.off_x);
+    double *red = reinterpret_cast<double *>(smem + lay.off_red);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j0 = a.panels[2 * blockIdx.x], ncols = a.panels[2 * blockIdx.x + 1];
+
+    // 1. bitmap of the rows present in the panel's columns
+    for (int64_t w = tid; w < a.nw; w += NT) bits[w] = make_uint2(0u, 0u);
+    __syncthreads();
+    for (int q = 0; q < ncols; ++q) {
+        const int64_t b = a.rp[j0 + q], e = a.rp[j0 + q + 1];
+        for (int64_t p = b + tid; p < e; p += NT) {
+            const int K = a.ci[p];
+            atomicOr(&bits[K >> 5].x, 1u << (K & 31));
+        }
+    }
+    __syncthreads();
+    const int64_t chunk = (a.nw + NT - 1) / NT;
+    const int64_t wb = min(a.nw, (int64_t)tid * chunk), we = min(a.nw, wb + chunk);
+    int cnt = 0;
+    for (int64_t w = wb; w < we; ++w) cnt += __popc(bits[w].x);
+    int total;
+    int run = block_excl_scan<NW>(cnt, wsum, &total);
+    if (tid == 0) s_nu = total;
+    for (int64_t w = wb; w < we; ++w) {
+        unsigned m = bits[w].x;
+        bits[w].y = (unsigned)run;
+        while (m) {
+            const int bpos = __ffs(m) - 1;
+            ulist[run++] = (int)(w * 32 + bpos);
+            m &= m - 1u;
+        }
+    }
+    const int nu = total;
+    if (nu > a.ucap) return;  // cannot happen for a plan-built launch (uniform exit)
+    // 2. gather the panel's columns of T_k
+    {
+        uint4 *x4 = reinterpret_cast<uint4 *>(X);
+        const int64_t n4 = (int64_t)nu * BB * P * sizeof(T) / 16;
+        for (int64_t i = tid; i < n4; i += NT) x4[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int64_t i = tid; i < (int64_t)nu * P; i += NT) pos[i] = -1;
+    }
+    __syncthreads();
+    for (int q = 0; q < ncols; ++q) {
+        const int64_t b = a.rp[j0 + q], e = a.rp[j0 + q + 1];
+        for (int64_t p = b + tid; p < e; p += NT) {
+            const int K = a.ci[p];
+            const int s = rank_of(bits, K);
+            T v[16];
+            load16<T>(v, a.R + (int64_t)a.tperm[p] * BB);
+            T *xs = X + (int64_t)s * BB * P;
+            const int sw = s & 1;
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) xs[((m ^ sw) * 4 * P) + 4 * q + c] = v[4 * m + c];
+            pos[s * P + q] = (int16_t)(p - b);
+        }
+    }
+    __syncthreads();
+
+    // 3.-4. rows of the union: masked block products, reduction, epilogue
+    const int q = lane % P, kg = lane / P;
+    double coefv[MAX_F];
+#pragma unroll
+    for (int f = 0; f < MAX_F; ++f) coefv[f] = f < a.nf ? a.coef[(int64_t)f * a.coef_stride + a.term] : 0.0;
+    double tpart = 0.0, gpart = 0.0;
+    for (int s = warp; s < nu; s += NW) {
+        const int I = ulist[s];
+        T acc[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[i] = T(0);
+        const int64_t a1 = a.Lrp[I + 1];
+        for (int64_t ai = a.Lrp[I] + kg; ai < a1; ai += KG) {
+            const int K = a.Lci[ai];
+            const int s2 = rank_of(bits, K);
+            if (s2 < 0) continue;
+            T h[16];
+            load16<T>(h, a.Lv + ai * BB);
+            const T *xs = X + (int64_t)s2 * BB * P + 4 * q;
+            const int sw = s2 & 1;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                T x[4];
+                lds4<T>(x, xs + (m ^ sw) * 4 * P);
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[4 * r + c] = fma(h[4 * r + m], x[c], acc[4 * r + c]);
+            }
+        }
+#pragma unroll
+        for (int o = P; o < 32; o <<= 1)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+        if (q < ncols && kg * EPL < 16) {
+            const int e = pos[s * P + q];
+            if (e >= 0) {
+                const int J = j0 + q;
+                const int64_t slot = (int64_t)a.tperm[a.rp[J] + e] * BB;
+                const bool diag = I == J;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    if (i / EPL != kg) continue;
+                    const int64_t idx = slot + i;
+                    T y = a.alpha * acc[i];
+                    if (a.Rm) y = y + a.beta * a.Rm[idx];
+                    a.C[idx] = y;
+                    const double yd = (double)y;
+#pragma unroll
+                    for (int f = 0; f < MAX_F; ++f)
+                        if (f < a.nf) a.acc[f][idx] += coefv[f] * yd;
+                    if (a.G) gpart += a.G[idx] * yd;
+                    if (diag && (i % 5) == 0) tpart += yd;
+                }
+            }
+        }
+    }
+    if (a.mom || a.gmom) {
+        double v[2] = {tpart, gpart};
+        double *const dst[2] = {a.mom, a.gmom};
+        finish_moments<NT, 2>(a.part, a.counter, v, dst, red);
+    }
+}
+
+// Terms 0 and 1: T_0 = I and T_1 = M~ on P_out, accumulators c_0/2 T_0 + c_1 T_1,
+// moments of both.  Same panel grid as the step kernel, so the partial buffer and
+// completion counter are shared.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_init(const int64_t *rp, const int32_t *ci, const int32_t *tperm,
+                                             const int32_t *panels, const int64_t *Lrp, const int32_t *Lci,
+                                             const double *Mt, T *T0, T *T1, int32_t nf, StepArgs<T> a,
+                                             double *mom, double *gmom) {
+    __shared__ double red[(NT / 32) * 4];
+    const int j0 = panels[2 * blockIdx.x], ncols = panels[2 * blockIdx.x + 1];
+    double c0[MAX_F], c1[MAX_F];
+#pragma unroll
+    for (int f = 0; f < MAX_F; ++f) {
+        c0[f] = f < nf ? a.coef[(int64_t)f * a.coef_stride + 0] : 0.0;
+        c1[f] = f < nf ? a.coef[(int64_t)f * a.coef_stride + 1] : 0.0;
+    }
+    double t0 = 0.0, t1 = 0.0, g0 = 0.0, g1 = 0.0;
+    for (int q = 0; q < ncols; ++q) {
+        const int J = j0 + q;
+        for (int64_t p = rp[J] + threadIdx.x; p < rp[J + 1]; p += NT) {
+            const int K = ci[p];  // block (K, J) of the column
+            const int64_t slot = (int64_t)tperm[p] * BB;
+            const int64_t la = find_in_row(Lrp, Lci, K, J);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const T v0 = (K == J && (i % 5) == 0) ? T(1) : T(0);
+                const T v1 = la >= 0 ? (T)Mt[la * BB + i] : T(0);
+                T0[slot + i] = v0;
+                T1[slot + i] = v1;
+                const double d0 = (double)v0, d1 = (double)v1;
+#pragma unroll
+                for (int f = 0; f < MAX_F; ++f)
+                    if (f < nf) a.acc[f][slot + i] = 0.5 * c0[f] * d0 + c1[f] * d1;
+                if (a.G) {
+                    g0 += a.G[slot + i] * d0;
+                    g1 += a.G[slot + i] * d1;
+                }
+                if (K == J && (i % 5) == 0) {
+                    t0 += d0;
+                    t1 += d1;
+                }
+            }
+        }
+    }
+    double v[4] = {t0, t1, g0, g1};
+    double *const dst[4] = {mom, mom ? mom + 1 : nullptr, gmom, gmom ? gmom + 1 : nullptr};
+    finish_moments<NT, 4>(a.part, a.counter, v, dst, red);
+}
+
+__global__ void k_to_f32(const double *in, float *out, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
+template <typename T, int P, int NW>
+int launch_step(const cheb_plan *plan, const StepArgs<T> &a, cudaStream_t s) {
+    const StepLayout lay = step_layout(a.nw, a.ucap, P, sizeof(T));
+    auto fn = k_step<T, P, NW>;
+    CHEB_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
+    fn<<<(unsigned)plan->n_panels, NW * 32, lay.total, s>>>(a);
+    return check_launch("k_step");
+}
+
+template <typename T>
+StepArgs<T> base_args(const cheb_plan *plan, const cheb_bsr *L, const T *Lv) {
+    StepArgs<T> a{};
+    a.nw = (plan->nbr + 31) / 32;
+    a.ucap = plan->max_union;
+    a.rp = plan->rp;
+    a.ci = plan->ci;
+    a.tperm = plan->d_tperm;
+    a.panels = plan->d_panels;
+    a.Lrp = L->row_ptr;
+    a.Lci = L->col_idx;
+    a.Lv = Lv;
+    return a;
+}
+
+constexpr int NW_F64 = 8, NW_F32 = 16;
+
+template <typename T>
+int run_step(const cheb_plan *plan, const StepArgs<T> &a, cudaStream_t s);
+template <>
+int run_step<double>(const cheb_plan *plan, const StepArgs<double> &a, cudaStream_t s) {
+    return launch_step<double, 2, NW_F64>(plan, a, s);
+}
+template <>
+int run_step<float>(const cheb_plan *plan, const StepArgs<float> &a, cudaStream_t s) {
+    return launch_step<float, 4, NW_F32>(plan, a, s);
+}
+
+size_t expand_ws(const cheb_plan *plan, int64_t nnzL, int precision) {
+    const size_t esz = precision == CHEB_F64 ? 8 : 4;
+    size_t b = 3 * align_up(plan->nnzb * BB * esz);
+    if (precision != CHEB_F64) b += align_up(nnzL * BB * esz);
+    b += align_up(plan->n_panels * 4 * sizeof(double)) + align_up(64);
+    return b + 256;
+}
+
+template <typename T>
+int expand_impl(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_terms, const double *coeffs,
+                int32_t stride, int32_t nf, double *const *acc, double *moments, const double *G,
+                double *gmoments, void *ws, size_t ws_bytes, cudaStream_t s) {
+    Carve cv(ws, ws_bytes);
+    T *buf[3];
+    for (int i = 0; i < 3; ++i) buf[i] = cv.take<T>(plan->nnzb * BB);
+    const T *Lv;
+    if (sizeof(T) == 8) {
+        Lv = reinterpret_cast<const T *>(Mt->vals);
+    } else {
+        float *lv = cv.take<float>(Mt->nnzb * BB);
+        int64_t n = Mt->nnzb * BB;
+        k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double *)Mt->vals, lv, n);
+        CHEB_TRY(check_launch("k_to_f32"));
+        Lv = reinterpret_cast<const T *>(lv);
+    }
+    double *part = cv.take<double>(plan->n_panels * 4);
+    int32_t *counter = cv.take<int32_t>(16);
+    if (!cv.fits()) return fail(CHEB_ERR_NOSPACE, "cheb_expand: workspace too small");
+    CHEB_CUDA(cudaMemsetAsync(counter, 0, 64, s));
+    StepArgs<T> a = base_args<T>(plan, Mt, Lv);
+    a.nf = nf;
+    for (int f = 0; f < nf; ++f) a.acc[f] = acc[f];
+    a.coef = coeffs;
+    a.coef_stride = stride;
+    a.G = G;
+    a.part = part;
+    a.counter = counter;
+    k_init<T, 256><<<(unsigned)plan->n_panels, 256, 0, s>>>(plan->rp, plan->ci, plan->d_tperm, plan->d_panels,
+                                                          Mt->row_ptr, Mt->col_idx, (const double *)Mt->vals,
+                                                          buf[0], buf[1], nf, a, moments, gmoments);
+    CHEB_TRY(check_launch("k_init"));
+    a.alpha = T(2);
+    a.beta = T(-1);
+    for (int k = 1; k + 1 < n_terms; ++k) {
+        a.R = buf[k % 3];
+        a.Rm = buf[(k - 1) % 3];
+        a.C = buf[(k + 1) % 3];
+        a.term = k + 1;
+        a.mom = moments ? moments + k + 1 : nullptr;
+        a.gmom = (gmoments && G) ? gmoments + k + 1 : nullptr;
+        CHEB_TRY(run_step<T>(plan, a, s));
+    }
+    return CHEB_OK;
+}
+
+}  // namespace cheb
+
+using namespace cheb;
+
+static int check_operator(const cheb_plan *plan, const cheb_bsr *Mt) {
+    if (!plan || !plan->bound) return fail(CHEB_ERR_INVALID, "plan is NULL or not bound");
+    if (!Mt || Mt->nbr != plan->nbr || !Mt->row_ptr || !Mt->col_idx || !Mt->vals || Mt->dtype != CHEB_F64)
+        return fail(CHEB_ERR_INVALID, "operator must be FP64 with the plan's block rows");
+    return CHEB_OK;
+}
+
+extern "C" int cheb_expand_workspace_size(const cheb_plan *plan, const cheb_bsr *Mt, int32_t precision,
+                                          size_t *bytes) {
+    if (!plan || !Mt || !bytes) return fail(CHEB_ERR_INVALID, "cheb_expand_workspace_size: NULL argument");
+    *bytes = expand_ws(plan, Mt->nnzb, precision);
+    return CHEB_OK;
+}
+
+extern "C" int cheb_expand(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_terms, const double *coeffs,
+                           int32_t coeff_stride, int32_t n_f, double *const *acc, double *moments,
+                           const double *G, double *gmoments, int32_t precision, void *ws, size_t ws_bytes,
+                           void *stream) {
+    CHEB_TRY(check_operator(plan, Mt));
+    if (n_terms < 2 || n_f < 0 || n_f > MAX_F || (n_f > 0 && (!acc || !coeffs)) || coeff_stride < n_terms)
+        return fail(CHEB_ERR_INVALID, "cheb_expand: bad n_terms / n_f / coefficients");
+    for (int f = 0; f < n_f; ++f)
+        if (!acc[f]) return fail(CHEB_ERR_INVALID, "cheb_expand: accumulator %d is NULL", f);
+    if (precision != plan->precision) return fail(CHEB_ERR_INVALID, "cheb_expand: plan precision differs");
+    if (!ws || ws_bytes < expand_ws(plan, Mt->nnzb, precision))
+        return fail(CHEB_ERR_NOSPACE, "cheb_expand: workspace %zu < %zu", ws_bytes,
+                    expand_ws(plan, Mt->nnzb, precision));
+    cudaStream_t s = as_stream(stream);
+    if (precision == CHEB_F64)
+        return expand_impl<double>(plan, Mt, n_terms, coeffs, coeff_stride, n_f, acc, moments, G, gmoments, ws,
+                                   ws_bytes, s);
+    if (precision == CHEB_F32)
+        return expand_impl<float>(plan, Mt, n_terms, coeffs, coeff_stride, n_f, acc, moments, G, gmoments, ws,
+                                  ws_bytes, s);
+    return fail(CHEB_ERR_INVALID, "cheb_expand: unsupported precision %d", precision);
+}
+
+extern "C" int cheb_masked_product(const cheb_plan *plan, const cheb_bsr *L, const double *R, double alpha,
+                                   const double *D, double beta, double *C, void *stream) {
+    CHEB_TRY(check_operator(plan, L));
+    if (plan->precision != CHEB_F64) return fail(CHEB_ERR_INVALID, "cheb_masked_product: needs an FP64 plan");
+    if (!R || !C || C == R || (D && C == D)) return fail(CHEB_ERR_INVALID, "cheb_masked_product: bad pointers");
+    StepArgs<double> a = base_args<double>(plan, L, (const double *)L->vals);
+    a.R = R;
+    a.Rm = D;
+    a.C = C;
+    a.alpha = alpha;
+    a.beta = D ? beta : 0.0;
+    a.nf = 0;
+    return run_step<double>(plan, a, as_stream(stream));
+}
+
+extern "C" int cheb_newton_schulz(const cheb_plan *plan, const cheb_bsr *S, const double *X0, double *X1,
+                                  double *tmp, void *stream) {
+    if (!S || !X0 || !X1 || !tmp || X1 == X0 || X1 == tmp || tmp == X0)
+        return fail(CHEB_ERR_INVALID, "cheb_newton_schulz: bad pointers");
+    CHEB_TRY(cheb_masked_product(plan, S, X0, 1.0, nullptr, 0.0, tmp, stream));
+    if (!plan) return CHEB_ERR_INVALID;
+    cheb_bsr Xb{plan->nbr, plan->nnzb, plan->rp, plan->ci, const_cast<double *>(X0), CHEB_F64};
+    return cheb_masked_product(plan, &Xb, tmp, -1.0, X0, 2.0, X1, stream);
+}

@@ -1,0 +1,147 @@
+// Plan creation (host C++): checks the output pattern, builds the block
+// transposition map and groups block columns into panels.
+//
+// Columns of the Chebyshev recursion are independent (Sec. "Expansion in
+// Chebyshev polynomials": each column of T_{k+1} needs only the same column of
+// T_k and T_{k-1}), so one thread block can advance a panel of P neighbouring
+// block columns with their row lists gathered in shared memory.  The panels are
+// formed greedily along the column order: a column joins the current panel while
+// the panel has fewer than P columns and the union of the panel's row lists
+// still fits the shared-memory budget.
+#include <algorithm>
+
+#include "common.cuh"
+#include "plan.cuh"
+
+using namespace cheb;
+
+static int union_capacity(int64_t nbr, int P, int esz) {
+    int64_t nw = (nbr + 31) / 32;
+    // largest ucap with step_layout(nw, ucap, P, esz).total <= budget
+    int lo = 0, hi = 1 << 16;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (step_layout(nw, mid, P, esz).total <= (size_t)CHEB_MAX_DYN_SMEM) lo = mid; else hi = mid - 1;
+    }
+    return std::min(lo, 32767);
+}
+
+extern "C" int cheb_plan_create(const cheb_bsr *P_out, int32_t precision, cheb_plan **out,
+                                size_t *plan_ws_bytes, void *stream) {
+    if (!out || !plan_ws_bytes) return fail(CHEB_ERR_INVALID, "cheb_plan_create: NULL output");
+    *out = nullptr;
+    if (!P_out || P_out->nbr < 1 || P_out->nnzb < P_out->nbr || !P_out->row_ptr || !P_out->col_idx)
+        return fail(CHEB_ERR_INVALID, "cheb_plan_create: bad pattern");
+    if (precision != CHEB_F64 && precision != CHEB_F32)
+        return fail(CHEB_ERR_INVALID, "cheb_plan_create: precision must be CHEB_F64 or CHEB_F32");
+    if (P_out->nnzb >= (int64_t)INT32_MAX) return fail(CHEB_ERR_INVALID, "cheb_plan_create: too many blocks");
+    const int64_t nbr = P_out->nbr, nnzb = P_out->nnzb;
+    std::vector<int64_t> rp(nbr + 1);
+    std::vector<int32_t> ci(nnzb);
+    cudaStream_t s = as_stream(stream);
+    CHEB_CUDA(cudaMemcpyAsync(rp.data(), P_out->row_ptr, (nbr + 1) * 8, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaMemcpyAsync(ci.data(), P_out->col_idx, nnzb * 4, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaStreamSynchronize(s));
+    if (rp[0] != 0 || rp[nbr] != nnzb) return fail(CHEB_ERR_INVALID, "cheb_plan_create: row_ptr does not span nnzb");
+    for (int64_t I = 0; I < nbr; ++I) {
+        if (rp[I + 1] < rp[I]) return fail(CHEB_ERR_INVALID, "row_ptr not monotone at row %lld", (long long)I);
+        bool diag = false;
+        for (int64_t p = rp[I]; p < rp[I + 1]; ++p) {
+            if (ci[p] < 0 || ci[p] >= nbr) return fail(CHEB_ERR_INVALID, "col_idx out of range in row %lld", (long long)I);
+            if (p > rp[I] && ci[p] <= ci[p - 1]) return fail(CHEB_ERR_INVALID, "col_idx not strictly ascending in row %lld", (long long)I);
+            diag |= ci[p] == I;
+        }
+        if (!diag) return fail(CHEB_ERR_INVALID, "diagonal block missing in row %lld", (long long)I);
+    }
+    auto plan = new cheb_plan();
+    plan->nbr = nbr;
+    plan->nnzb = nnzb;
+    plan->rp = P_out->row_ptr;
+    plan->ci = P_out->col_idx;
+    plan->precision = precision;
+    plan->h_tperm.resize(nnzb);
+    for (int64_t I = 0; I < nbr; ++I) {
+        for (int64_t p = rp[I]; p < rp[I + 1]; ++p) {
+            const int32_t J = ci[p];
+            auto b = ci.begin() + rp[J], e = ci.begin() + rp[J + 1];
+            auto it = std::lower_bound(b, e, (int32_t)I);
+            if (it == e || *it != I) {
+                delete plan;
+                return fail(CHEB_ERR_INVALID, "pattern not symmetric: (%lld,%d) present, transpose missing",
+                            (long long)I, J);
+            }
+            plan->h_tperm[p] = (int32_t)(it - ci.begin());
+        }
+    }
+    const int P = panel_width_for(precision);
+    const int esz = precision == CHEB_F64 ? 8 : 4;
+    plan->P = P;
+    plan->ucap = union_capacity(nbr, P, esz);
+    // greedy panels; stamp[K] = last panel that counted row K
+    std::vector<int32_t> stamp(nbr, -1);
+    int64_t j = 0, panel = 0;
+    int32_t max_union = 0;
+    while (j < nbr) {
+        int32_t cnt = 0, ncols = 0;
+        const int64_t j0 = j;
+        while (j < nbr && ncols < P) {
+            // rows of column j (= columns of row j, the pattern being symmetric)
+            int32_t add = 0;
+            for (int64_t p = rp[j]; p < rp[j + 1]; ++p) add += stamp[ci[p]] != (int32_t)panel;
+            if (ncols > 0 && cnt + add > plan->ucap) break;
+            if (cnt + add > plan->ucap) {
+                delete plan;
+                return fail(CHEB_ERR_NOSPACE, "column %lld has %d rows, shared-memory panel holds %d",
+                            (long long)j, add, plan->ucap);
+            }
+            for (int64_t p = rp[j]; p < rp[j + 1]; ++p) stamp[ci[p]] = (int32_t)panel;
+            cnt += add;
+            ++ncols;
+            ++j;
+        }
+        plan->h_panels.push_back((int32_t)j0);
+        plan->h_panels.push_back(ncols);
+        max_union = std::max(max_union, cnt);
+        ++panel;
+    }
+    plan->n_panels = panel;
+    plan->max_union = max_union;
+    plan->ws_bytes = align_up(nnzb * 4) + align_up(plan->h_panels.size() * 4) + align_up(64);
+    *plan_ws_bytes = plan->ws_bytes;
+    *out = plan;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_bind(cheb_plan *plan, void *ws, size_t ws_bytes, void *stream) {
+    if (!plan) return fail(CHEB_ERR_INVALID, "cheb_plan_bind: NULL plan");
+    if (!ws || ws_bytes < plan->ws_bytes)
+        return fail(CHEB_ERR_NOSPACE, "cheb_plan_bind: workspace %zu < %zu", ws_bytes, plan->ws_bytes);
+    if (((uintptr_t)ws) % 256) return fail(CHEB_ERR_INVALID, "cheb_plan_bind: workspace not 256-byte aligned");
+    Carve cv(ws, ws_bytes);
+    plan->d_tperm = cv.take<int32_t>(plan->nnzb);
+    plan->d_panels = cv.take<int32_t>(plan->h_panels.size());
+    plan->d_counter = cv.take<int32_t>(16);
+    cudaStream_t s = as_stream(stream);
+    CHEB_CUDA(cudaMemcpyAsync(plan->d_tperm, plan->h_tperm.data(), plan->nnzb * 4, cudaMemcpyHostToDevice, s));
+    CHEB_CUDA(cudaMemcpyAsync(plan->d_panels, plan->h_panels.data(), plan->h_panels.size() * 4,
+                              cudaMemcpyHostToDevice, s));
+    CHEB_CUDA(cudaMemsetAsync(plan->d_counter, 0, 64, s));
+    // The host vectors are read by the async copies: finish them before returning.
+    CHEB_CUDA(cudaStreamSynchronize(s));
+    plan->bound = true;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_info(const cheb_plan *plan, int64_t *n_panels, int32_t *panel_width,
+                              int32_t *max_union) {
+    if (!plan) return fail(CHEB_ERR_INVALID, "cheb_plan_info: NULL plan");
+    if (n_panels) *n_panels = plan->n_panels;
+    if (panel_width) *panel_width = plan->P;
+    if (max_union) *max_union = plan->max_union;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_destroy(cheb_plan *plan) {
+    delete plan;
+    return CHEB_OK;
+}

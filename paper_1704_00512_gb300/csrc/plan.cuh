@@ -1,0 +1,62 @@
+// The plan object: transposition map and column panels of a symmetric output pattern.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+// Largest dynamic shared memory a block may use on sm_100/sm_103 (227 KB).
+#define CHEB_MAX_DYN_SMEM 232448
+
+struct cheb_plan {
+    int64_t nbr = 0;
+    int64_t nnzb = 0;
+    const int64_t *rp = nullptr;  // device, caller-owned pattern of P_out
+    const int32_t *ci = nullptr;
+    int32_t precision = CHEB_F64;
+    int32_t P = 1;          // panel width (block columns advanced by one thread block)
+    int64_t n_panels = 0;
+    int32_t max_union = 0;  // largest union of row lists over a panel
+    int32_t ucap = 0;       // union rows that fit in shared memory
+    std::vector<int32_t> h_tperm;   // slot of (J,I) for each slot (I,J)
+    std::vector<int32_t> h_panels;  // pairs (first column, column count)
+    // device copies after cheb_plan_bind
+    bool bound = false;
+    int32_t *d_tperm = nullptr;
+    int32_t *d_panels = nullptr;
+    int32_t *d_counter = nullptr;  // grid-completion counter used by the step kernel
+    size_t ws_bytes = 0;
+};
+
+namespace cheb {
+
+// Shared-memory layout of the step kernel for a panel of width P over a union of
+// ucap rows, element size esz, nw bitmap words.
+struct StepLayout {
+    size_t off_bits, off_ulist, off_pos, off_x, off_red, total;
+};
+
+__host__ __device__ inline StepLayout step_layout(int64_t nw, int64_t ucap, int P, int esz) {
+    StepLayout L;
+    size_t o = 0;
+    L.off_bits = o;
+    o += (size_t)nw * 8;  // uint2 {bitmap word, prefix count}
+    o = (o + 15) / 16 * 16;
+    L.off_ulist = o;
+    o += (size_t)ucap * 4;
+    o = (o + 15) / 16 * 16;
+    L.off_pos = o;
+    o += (size_t)ucap * P * 2;  // int16 position of the row within each panel column
+    o = (o + 15) / 16 * 16;
+    L.off_x = o;
+    o += (size_t)ucap * BB * P * esz;  // the gathered panel of T_k
+    o = (o + 15) / 16 * 16;
+    L.off_red = o;
+    o += 64 * 8;  // per-warp moment partials (<= 32 warps x 2)
+    L.total = o;
+    return L;
+}
+
+inline int panel_width_for(int precision) { return precision == CHEB_F64 ? 2 : 4; }
+
+}  // namespace cheb

@@ -1,0 +1,184 @@
+"""Solve sequences built from the C ABI (every numerical step runs in libcheb.so).
+
+``powers_solve``: matrix powers S^a from one shared recursion (Sec. "Matrix
+powers"), optionally followed by one FP64 Newton-Schulz step for S^-1.
+
+``foe_solve``: the Fermi-operator expansion with the S^-1/2 transformation and
+the mu search (Sec. "Fermi Operator Expansion"):
+  1. block patterns P_H (cutoff r_c) and P_out (r_c + r_buf) from the atoms;
+  2. S^-1/2 by a power expansion of S on P_out;
+  3. H' = P_H(S^-1/2 P_out(H S^-1/2));
+  4. Lanczos bounds of H', degree for the occupation function at the interval
+     centre (the hardest position for a Chebyshev fit);
+  5. pass 1: the recursion on H~' with the trace functional g_k = <T_k, G>,
+     G = (P_out(S^-1/2 P_out(S S^-1/2)))^T, so that Tr(F(mu) S) = sum_k c_k(mu) g_k;
+  6. bisection for Tr(F S) = N_e on g (no new products);
+  7. pass 2: the recursion again, accumulating p at mu*;
+  8. F = P_out(S^-1/2 P_out(p S^-1/2)) and Tr(F S).
+Host code only sequences calls and moves a few scalars (bounds, degree, mu).
+"""
+
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _bsr_to_device(row_ptr, col_idx, vals, device) -> L.Bsr:
+    return L.Bsr(torch.as_tensor(row_ptr, dtype=torch.int64, device=device),
+                 torch.as_tensor(col_idx, dtype=torch.int32, device=device),
+                 None if vals is None else torch.as_tensor(np.ascontiguousarray(vals), dtype=torch.float64,
+                                                          device=device))
+
+
+class Problem:
+    """Device-resident inputs of one system: atoms, P_H with S and H, and P_out."""
+
+    def __init__(self, xyz: np.ndarray, L_box: float, r_c: float, r_buf: float, S_vals: np.ndarray,
+                 H_vals: np.ndarray, device, precision: int = L.F64):
+        self.device = torch.device(device)
+        self.L = float(L_box)
+        self.r_c = float(r_c)
+        self.r_out = float(r_c + r_buf)
+        self.xyz = torch.as_tensor(np.ascontiguousarray(xyz), dtype=torch.float64, device=self.device)
+        self.S_host = S_vals
+        self.H_host = H_vals
+        self.precision = precision
+        self.build_patterns()
+        self.S = self.P_H.with_vals(torch.as_tensor(np.ascontiguousarray(S_vals), dtype=torch.float64,
+                                                    device=self.device))
+        self.H = self.P_H.with_vals(torch.as_tensor(np.ascontiguousarray(H_vals), dtype=torch.float64,
+                                                    device=self.device))
+
+    def build_patterns(self):
+        rp, ci = L.pattern_build(self.xyz, self.L, self.r_c)
+        self.P_H = L.Bsr(rp, ci)
+        rp, ci = L.pattern_build(self.xyz, self.L, self.r_out)
+        self.P_out = L.Bsr(rp, ci)
+        self.plan64 = L.Plan(self.P_out, L.F64)
+        self.planX = self.plan64 if self.precision == L.F64 else L.Plan(self.P_out, self.precision)
+
+    @property
+    def n_rows(self) -> int:
+        return 4 * (self.P_H.nbr)
+
+    def zeros_out(self) -> torch.Tensor:
+        return torch.zeros((self.P_out.nnzb, 4, 4), dtype=torch.float64, device=self.device)
+
+
+def problem_from_system(sysm, r_buf: float, device, precision: int = L.F64) -> Problem:
+    return Problem(sysm.xyz, sysm.L, sysm.r_cut, r_buf, sysm.S, sysm.H, device, precision)
+
+
+def powers(pb: Problem, exponents=(-1.0, 0.5, -0.5), tol: float = 1e-10, n_max: int = 512,
+           lanczos_k: int = 40, bounds_S=None, n_terms=None, newton_schulz: bool = False,
+           precision: int | None = None) -> dict:
+    """S^a for every a in exponents from one recursion on S~ (Sec. "Matrix powers")."""
+    prec = pb.precision if precision is None else precision
+    plan = pb.plan64 if prec == L.F64 else pb.planX
+    if bounds_S is None:
+        e0, e1, th = L.bounds(pb.S, lanczos_k)
+        if th[0] <= 0:
+            raise L.ChebError(L.ERR_NOT_SPD, f"Lanczos lower Ritz value {th[0]} <= 0")
+        e0 = max(e0, 0.5 * th[0])
+    else:
+        e0, e1 = bounds_S
+    St = pb.S.with_vals(L.scale(pb.S, e0, e1))
+    funcs = [{"kind": L.POWER, "a": a} for a in exponents]
+    if n_terms is None:
+        n, c = L.coeffs(funcs, e0, e1, tol, n_max, rel=True, device=pb.device)
+    else:
+        n, c = L.coeffs(funcs, e0, e1, 0.0, n_terms, device=pb.device)
+    accs = [pb.zeros_out() for _ in exponents]
+    t = torch.zeros(n, dtype=torch.float64, device=pb.device)
+    L.expand(plan, St, n, c, accs, moments=t, precision=prec)
+    out = {"bounds": (e0, e1), "n_terms": n, "coeffs": c, "acc": accs, "moments": t}
+    if newton_schulz and -1.0 in exponents:
+        X0 = accs[list(exponents).index(-1.0)]
+        X1 = pb.zeros_out()
+        tmp = pb.zeros_out()
+        L.newton_schulz(pb.plan64, pb.S, X0, X1, tmp)
+        out["inv_ns"] = X1
+    return out
+
+
+def orthogonalise(pb: Problem, A: torch.Tensor) -> L.Bsr:
+    """H' = P_H(A P_out(H A)), A = S^-1/2 on P_out."""
+    Y = pb.zeros_out()
+    Z = pb.zeros_out()
+    L.masked_product(pb.plan64, pb.H, A, Y)
+    L.masked_product(pb.plan64, pb.P_out.with_vals(A), Y, Z)
+    return pb.P_H.with_vals(L.restrict(pb.P_out.with_vals(Z), pb.P_H))
+
+
+def trace_functional(pb: Problem, A: torch.Tensor) -> torch.Tensor:
+    """G with <X, G> = Tr(P_out(A P_out(X A)) S): the transpose of P_out(A P_out(S A))."""
+    Y = pb.zeros_out()
+    Z = pb.zeros_out()
+    L.masked_product(pb.plan64, pb.S, A, Y)
+    L.masked_product(pb.plan64, pb.P_out.with_vals(A), Y, Z)
+    return L.transpose(pb.plan64, Z)
+
+
+def postprocess(pb: Problem, A: torch.Tensor, p: torch.Tensor) -> torch.Tensor:
+    """F = P_out(A P_out(p A))."""
+    Y = pb.zeros_out()
+    F = pb.zeros_out()
+    L.masked_product(pb.plan64, pb.P_out.with_vals(p), A, Y)
+    L.masked_product(pb.plan64, pb.P_out.with_vals(A), Y, F)
+    return F
+
+
+def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FERMI, n_max: int = 16384,
+        lanczos_k: int = 40, tol_N: float | None = None, bounds_S=None, n_S=None, bounds_H=None, n_H=None,
+        max_iter: int = 100, timings: dict | None = None) -> dict:
+    """Density matrix F with Tr(F S) = N_e (see the module docstring for the steps)."""
+    tm = {} if timings is None else timings
+    t0 = time.perf_counter()
+    pw = powers(pb, exponents=(-0.5,), tol=tol, bounds_S=bounds_S, n_terms=n_S, precision=L.F64)
+    A = pw["acc"][0]
+    Hp = orthogonalise(pb, A)
+    if bounds_H is None:
+        e0, e1, _ = L.bounds(Hp, lanczos_k)
+    else:
+        e0, e1 = bounds_H
+    Hpt = Hp.with_vals(L.scale(Hp, e0, e1))
+    G = trace_functional(pb, A)
+    mid = 0.5 * (e0 + e1)
+    if n_H is None:
+        n, _ = L.coeffs([{"kind": kind, "mu": mid, "kT": kT}], e0, e1, tol, n_max, device=pb.device)
+    else:
+        n = n_H
+    tm["setup_s"] = time.perf_counter() - t0
+    t = torch.zeros(n, dtype=torch.float64, device=pb.device)
+    g = torch.zeros(n, dtype=torch.float64, device=pb.device)
+    ws = L.expand(pb.planX, Hpt, n, None, [], moments=t, G=G, gmoments=g, precision=pb.precision)
+    if tol_N is None:
+        tol_N = 1e-9 * N_e if pb.precision == L.F64 else 1e-6 * N_e
+    res = L.mu_search(g, n, e0, e1, kind, kT, N_e, tol_N, max_iter)
+    r = L.decode_mu_result(res)
+    mu = r["mu"]
+    _, c = L.coeffs([{"kind": kind, "mu": mu, "kT": kT}], e0, e1, 0.0, n, device=pb.device)
+    p = pb.zeros_out()
+    L.expand(pb.planX, Hpt, n, c, [p], precision=pb.precision, ws=ws)
+    F = postprocess(pb, A, p)
+    trFS = L.trace(pb.P_out.with_vals(F), pb.S)
+    return {"F": F, "p": p, "A": A, "Hp": Hp, "G": G, "mu": mu, "mu_result": r, "moments": t, "gmoments": g,
+            "n_terms": n, "bounds_H": (e0, e1), "bounds_S": pw["bounds"], "n_S": pw["n_terms"],
+            "trace_FS": trFS}
+
+
+def foe_solve(sysm, r_buf: float, kT: float, N_e: float, tol: float = 1e-10, precision: int = L.F64,
+              device="cuda", **kw) -> dict:
+    """foe() on a synthetic system, with host copies of the main results."""
+    pb = problem_from_system(sysm, r_buf, device, precision)
+    out = foe(pb, kT, N_e, tol=tol, **kw)
+    torch.cuda.synchronize(pb.device)
+    out["problem"] = pb
+    out["F_host"] = out["F"].cpu().numpy()
+    out["trace_FS"] = float(out["trace_FS"].item())
+    return out

@@ -1,0 +1,318 @@
+"""GPU parity: every C-ABI call against the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances: integer work (patterns, mu decisions, degrees) must be identical;
+FP64 values must match to relative Frobenius 1e-10 (rounding-order differences
+only); the FP32 recursion is compared against FP64 with the bound derived in
+test_expand_fp32_error_bound.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import pipelines, ref
+
+pytestmark = pytest.mark.gpu
+
+cg = pytest.importorskip("paper_1704_00512_gb300")
+from paper_1704_00512_gb300 import solve  # noqa: E402
+
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+if DEV is None:
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def relF(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dbsr(row_ptr, col_idx, vals=None):
+    return cg.Bsr(torch.as_tensor(row_ptr, dtype=torch.int64, device=DEV),
+                  torch.as_tensor(col_idx, dtype=torch.int32, device=DEV),
+                  None if vals is None else torch.as_tensor(np.ascontiguousarray(vals), dtype=torch.float64,
+                                                           device=DEV))
+
+
+def setup(n_atoms, r_c, r_buf, seed):
+    s = synth.make_system(n_atoms, r_c, seed)
+    S, H, P_out = pipelines.system_mats(s, r_buf)
+    return s, S, H, P_out
+
+
+# --------------------------------------------------------------------------
+# A1 patterns: bit-exact
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_atoms,r", [(1, 5.0), (7, 3.0), (200, 8.0), (200, 12.0), (1000, 10.0), (3000, 14.0)])
+def test_pattern_build_exact(n_atoms, r):
+    xyz, L = synth.place_atoms(n_atoms, seed=n_atoms)
+    rp, ci = cg.pattern_build(torch.as_tensor(xyz, device=DEV), L, r)
+    orp, oci = ref.pattern(xyz, L, r)
+    assert np.array_equal(rp.cpu().numpy(), orp)
+    assert np.array_equal(ci.cpu().numpy(), oci)
+
+
+def test_pattern_build_boundary_distances_exact():
+    # atoms at exactly representable distances on the cutoff
+    xyz = np.array([[0.0, 0.0, 0.0], [2.0, 0.0, 0.0], [0.0, 2.0, 0.0], [9.0, 9.0, 9.0], [1.0, 1.0, 1.0]])
+    for r in (2.0, np.sqrt(3.0), 1.9999999999999998):
+        rp, ci = cg.pattern_build(torch.as_tensor(xyz, device=DEV), 10.0, float(r))
+        orp, oci = ref.pattern(xyz, 10.0, float(r))
+        assert np.array_equal(rp.cpu().numpy(), orp) and np.array_equal(ci.cpu().numpy(), oci)
+
+
+# --------------------------------------------------------------------------
+# elementwise helpers
+# --------------------------------------------------------------------------
+
+def test_scale_transpose_restrict_trace():
+    s, S, H, P_out = setup(60, 4.0, 2.0, 1)
+    dH = dbsr(s.row_ptr, s.col_idx, s.H)
+    got = cg.scale(dH, -3.0, 2.5).cpu().numpy()
+    want = ref.scale(H, -3.0, 2.5).vals
+    assert np.max(np.abs(got - want)) == 0.0
+    rng = np.random.default_rng(0)
+    X = P_out.with_vals(rng.normal(size=(P_out.nnzb, 4, 4)))
+    dP = dbsr(P_out.row_ptr, P_out.col_idx, X.vals)
+    plan = cg.Plan(dP, cg.F64)
+    assert np.array_equal(cg.transpose(plan, dP.vals).cpu().numpy(), ref.transpose(X).vals)
+    dS = dbsr(s.row_ptr, s.col_idx, s.S)
+    r = cg.restrict(dP, dS).cpu().numpy()
+    assert np.array_equal(r, ref.restrict(X, S).vals)
+    tr = cg.trace(dP, dS).item()
+    assert abs(tr - ref.trace_product(X, S)) < 1e-12 * abs(tr) + 1e-12
+
+
+# --------------------------------------------------------------------------
+# masked products: several panels, ragged tail, both left patterns
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_atoms,r_c,r_buf", [(33, 3.0, 1.5), (150, 5.0, 3.0), (600, 8.0, 4.0)])
+def test_masked_product_fp64(n_atoms, r_c, r_buf):
+    s, S, H, P_out = setup(n_atoms, r_c, r_buf, n_atoms)
+    rng = np.random.default_rng(n_atoms)
+    R = rng.normal(size=(P_out.nnzb, 4, 4))
+    D = rng.normal(size=(P_out.nnzb, 4, 4))
+    dP = dbsr(P_out.row_ptr, P_out.col_idx)
+    plan = cg.Plan(dP, cg.F64)
+    npan, width, mu = plan.info()
+    assert width == 2 and npan >= (n_atoms + 1) // 2
+    dR = torch.as_tensor(R, device=DEV)
+    dD = torch.as_tensor(D, device=DEV)
+    for Lm in (H, P_out.with_vals(rng.normal(size=(P_out.nnzb, 4, 4)))):
+        dL = dbsr(Lm.row_ptr, Lm.col_idx, Lm.vals)
+        C = torch.empty_like(dR)
+        cg.masked_product(plan, dL, dR, C, alpha=2.0, D=dD, beta=-1.0)
+        want = 2.0 * ref.masked_product(Lm, P_out.with_vals(R), P_out.row_ptr, P_out.col_idx) - D
+        assert relF(C.cpu().numpy(), want) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# the fused recursion
+# --------------------------------------------------------------------------
+
+def _expand_case(n_atoms, r_c, r_buf, seed, n, nf):
+    s, S, H, P_out = setup(n_atoms, r_c, r_buf, seed)
+    w = np.linalg.eigvalsh(H.dense()) if n_atoms <= 300 else None
+    e0, e1 = (w[0] - 0.05, w[-1] + 0.05) if w is not None else (-12.0, 12.0)
+    Ht = ref.scale(H, e0, e1)
+    rng = np.random.default_rng(seed)
+    coeffs = rng.normal(size=(nf, n)) / (1.0 + np.arange(n)) ** 1.5
+    G = P_out.with_vals(rng.normal(size=(P_out.nnzb, 4, 4)))
+    return s, H, P_out, e0, e1, Ht, coeffs, G
+
+
+@pytest.mark.parametrize("n_atoms,r_c,r_buf,n,nf", [(33, 3.0, 1.5, 40, 1), (120, 4.0, 2.0, 64, 3),
+                                                     (400, 6.0, 3.0, 30, 8)])
+def test_expand_fp64_parity(n_atoms, r_c, r_buf, n, nf):
+    s, H, P_out, e0, e1, Ht, coeffs, G = _expand_case(n_atoms, r_c, r_buf, n_atoms + 1, n, nf)
+    ex = ref.chebyshev_expand(Ht, P_out, coeffs, G=G)
+    dP = dbsr(P_out.row_ptr, P_out.col_idx)
+    plan = cg.Plan(dP, cg.F64)
+    dHt = dbsr(Ht.row_ptr, Ht.col_idx, Ht.vals)
+    acc = [torch.zeros((P_out.nnzb, 4, 4), dtype=torch.float64, device=DEV) for _ in range(nf)]
+    t = torch.zeros(n, dtype=torch.float64, device=DEV)
+    g = torch.zeros(n, dtype=torch.float64, device=DEV)
+    cg.expand(plan, dHt, n, torch.as_tensor(coeffs, device=DEV), acc, moments=t,
+              G=torch.as_tensor(G.vals, device=DEV), gmoments=g, precision=cg.F64)
+    for j in range(nf):
+        assert relF(acc[j].cpu().numpy(), ex.acc[j].vals) < 1e-10
+    assert relF(t.cpu().numpy(), ex.t) < 1e-10
+    assert relF(g.cpu().numpy(), ex.g) < 1e-10
+
+
+def test_expand_deterministic_and_moments_only():
+    s, H, P_out, e0, e1, Ht, coeffs, G = _expand_case(120, 4.0, 2.0, 5, 50, 2)
+    dP = dbsr(P_out.row_ptr, P_out.col_idx)
+    plan = cg.Plan(dP, cg.F64)
+    dHt = dbsr(Ht.row_ptr, Ht.col_idx, Ht.vals)
+    dG = torch.as_tensor(G.vals, device=DEV)
+    outs = []
+    for _ in range(2):
+        acc = [torch.zeros((P_out.nnzb, 4, 4), dtype=torch.float64, device=DEV) for _ in range(2)]
+        g = torch.zeros(50, dtype=torch.float64, device=DEV)
+        cg.expand(plan, dHt, 50, torch.as_tensor(coeffs, device=DEV), acc, G=dG, gmoments=g)
+        outs.append((acc[0].cpu().numpy(), g.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    g2 = torch.zeros(50, dtype=torch.float64, device=DEV)
+    cg.expand(plan, dHt, 50, None, [], G=dG, gmoments=g2)
+    assert np.array_equal(g2.cpu().numpy(), outs[0][1])
+
+
+def test_expand_fp32_error_bound():
+    # FP32 T_k: each step adds a rounding of relative size u = 2^-24 to a term
+    # whose norm stays O(1) in the scaled spectrum; a perturbation at step j
+    # reaches T_k through U_{k-j} (|U_m| <= m+1), so the accumulated error of
+    # sum c_k T_k is below u * sum_k |c_k| * k^2 (up to a modest constant).
+    n, nf = 64, 2
+    s, H, P_out, e0, e1, Ht, coeffs, G = _expand_case(150, 4.0, 2.0, 9, n, nf)
+    ex = ref.chebyshev_expand(Ht, P_out, coeffs, G=G)
+    dP = dbsr(P_out.row_ptr, P_out.col_idx)
+    plan = cg.Plan(dP, cg.F32)
+    dHt = dbsr(Ht.row_ptr, Ht.col_idx, Ht.vals)
+    acc = [torch.zeros((P_out.nnzb, 4, 4), dtype=torch.float64, device=DEV) for _ in range(nf)]
+    g = torch.zeros(n, dtype=torch.float64, device=DEV)
+    cg.expand(plan, dHt, n, torch.as_tensor(coeffs, device=DEV), acc, G=torch.as_tensor(G.vals, device=DEV),
+              gmoments=g, precision=cg.F32)
+    u = 2.0 ** -24
+    k = np.arange(n)
+    for j in range(nf):
+        bound = 8 * u * np.sum(np.abs(coeffs[j]) * (1 + k) ** 2) * np.sqrt(P_out.nnzb * 16)
+        err = np.linalg.norm(acc[j].cpu().numpy() - ex.acc[j].vals)
+        assert err < bound, (err, bound)
+        assert relF(acc[j].cpu().numpy(), ex.acc[j].vals) < 1e-4
+
+
+# --------------------------------------------------------------------------
+# coefficients and degree (Eq. 4, Eq. 6)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("func,emin,emax,tol,rel", [
+    ({"kind": 0, "mu": 0.1, "kT": 0.05}, -2.0, 3.0, 1e-10, False),
+    ({"kind": 1, "mu": -0.3, "kT": 0.1}, -2.0, 3.0, 1e-9, False),
+    ({"kind": 2, "a": -1.0}, 0.05, 3.0, 1e-10, True),
+    ({"kind": 2, "a": 0.5}, 0.05, 3.0, 1e-10, True),
+    ({"kind": 2, "a": -0.5}, 0.05, 3.0, 1e-10, True),
+    ({"kind": 3, "lo": -0.5, "hi": 0.7, "kT": 0.05}, -2.0, 3.0, 1e-8, False),
+])
+def test_coeffs_and_degree_parity(func, emin, emax, tol, rel):
+    n, c = cg.coeffs([func], emin, emax, tol, 4096, rel=rel, device=DEV)
+    f = ref.Func(func["kind"], mu=func.get("mu", 0.0), kT=func.get("kT", 0.0), a=func.get("a", 0.0),
+                 lo=func.get("lo", 0.0), hi=func.get("hi", 0.0))
+    assert n == ref.choose_degree(f, emin, emax, tol, 4096, rel=rel)
+    want = ref.cheb_coeffs(f, n, emin, emax)
+    got = c.cpu().numpy()[0]
+    assert np.max(np.abs(got[:n] - want)) < 1e-13 * max(1.0, np.max(np.abs(want)))
+    assert np.all(got[n:] == 0)
+
+
+def test_coeffs_several_functions_take_largest_degree():
+    fs = [{"kind": 0, "mu": 0.0, "kT": 0.2}, {"kind": 0, "mu": 0.0, "kT": 0.05}]
+    n, c = cg.coeffs(fs, -2.0, 2.0, 1e-10, 8192, device=DEV)
+    n2 = max(ref.choose_degree(ref.Func(0, mu=0.0, kT=f["kT"]), -2.0, 2.0, 1e-10, 8192) for f in fs)
+    assert n == n2
+    with pytest.raises(cg.ChebError) as e:
+        cg.coeffs([{"kind": 0, "mu": 0.0, "kT": 1e-4}], -2.0, 2.0, 1e-10, 64, device=DEV)
+    assert e.value.code == 5
+
+
+def test_penalty_trace_parity():
+    rng = np.random.default_rng(3)
+    t = rng.normal(size=300)
+    got = cg.penalty_trace(torch.as_tensor(t, device=DEV), 300, -100.0).item()
+    want = ref.penalty_trace(t, -100.0, -1.0, 1.0)
+    assert abs(got - want) < 1e-12 * max(1.0, abs(want))
+
+
+# --------------------------------------------------------------------------
+# Lanczos bounds
+# --------------------------------------------------------------------------
+
+def test_bounds_parity_and_containment():
+    s, S, H, P_out = setup(300, 6.0, 3.0, 4)
+    for M in (S, H):
+        dM = dbsr(M.row_ptr, M.col_idx, M.vals)
+        e0, e1, th = cg.bounds(dM, 40)
+        a, b = ref.lanczos(M, pipelines.lanczos_start(4 * 300), 40)
+        o0, o1, oth0, oth1 = ref.ritz_bounds(a, b)
+        w = np.linalg.eigvalsh(M.dense())
+        width = w[-1] - w[0]
+        assert e0 <= w[0] and e1 >= w[-1]
+        assert abs(th[0] - oth0) < 1e-9 * width and abs(th[1] - oth1) < 1e-9 * width
+        # margins depend on tiny Ritz residuals; agree to the 1e-6 of the width
+        assert abs(e0 - o0) < 1e-6 * width and abs(e1 - o1) < 1e-6 * width
+
+
+# --------------------------------------------------------------------------
+# mu search, Newton-Schulz, whole solves
+# --------------------------------------------------------------------------
+
+def test_mu_search_decisions_match():
+    s, S, H, P_out = setup(40, 3.0, 1.5, 6)
+    w = np.linalg.eigvalsh(H.dense())
+    e0, e1 = w[0] - 0.1, w[-1] + 0.1
+    n = 400
+    Ht = ref.scale(H, e0, e1)
+    ex = ref.chebyshev_expand(Ht, P_out, np.zeros((1, n)), G=ref.identity(P_out))
+    N_e = 80.0
+    for kind in (0, 1):
+        want = ref.mu_bisect(ex.g, kind, 0.05, e0, e1, N_e, 1e-9 * N_e)
+        res = cg.decode_mu_result(cg.mu_search(torch.as_tensor(ex.g, device=DEV), n, e0, e1, kind, 0.05, N_e,
+                                               1e-9 * N_e))
+        assert res["converged"] == want.converged and res["iters"] == want.iters
+        assert res["bits"] == want.bits
+        assert abs(res["mu"] - want.mu) <= 1e-15 * max(1.0, abs(want.mu))
+
+
+def test_newton_schulz_parity():
+    s, S, H, P_out = setup(150, 5.0, 3.0, 7)
+    rng = np.random.default_rng(1)
+    X0 = P_out.with_vals(rng.normal(size=(P_out.nnzb, 4, 4)) * 0.1)
+    want = ref.newton_schulz(S, X0, P_out).vals
+    dP = dbsr(P_out.row_ptr, P_out.col_idx)
+    plan = cg.Plan(dP, cg.F64)
+    dX0 = torch.as_tensor(X0.vals, device=DEV)
+    X1, tmp = torch.empty_like(dX0), torch.empty_like(dX0)
+    cg.newton_schulz(plan, dbsr(s.row_ptr, s.col_idx, s.S), dX0, X1, tmp)
+    assert relF(X1.cpu().numpy(), want) < 1e-12
+
+
+def test_powers_solve_parity():
+    s, S, H, P_out = setup(300, 6.0, 3.0, 8)
+    pb = solve.problem_from_system(s, 3.0, DEV)
+    out = solve.powers(pb, exponents=(-1.0, 0.5, -0.5), tol=1e-10, n_max=512, newton_schulz=True)
+    orc = pipelines.powers(S, P_out, (-1.0, 0.5, -0.5), out["bounds"], out["n_terms"], newton_schulz=True)
+    for j in range(3):
+        assert relF(out["acc"][j].cpu().numpy(), orc["acc"][j].vals) < 1e-10
+    assert relF(out["inv_ns"].cpu().numpy(), orc["inv_ns"].vals) < 1e-10
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_foe_solve_parity(kind):
+    s, S, H, P_out = setup(48, 3.5, 1.5, 10)
+    N_e = float(s.n_rows // 2)
+    out = solve.foe_solve(s, 1.5, kT=0.08, N_e=N_e, tol=1e-9, kind=kind, device=DEV)
+    orc = pipelines.foe(S, H, P_out, 0.08, N_e, out["bounds_S"], out["n_S"], out["bounds_H"], out["n_terms"],
+                        tol_N=1e-9 * N_e, kind=kind)
+    r = out["mu_result"]
+    assert r["converged"] and orc["mu"].converged
+    assert r["bits"] == orc["mu"].bits and r["iters"] == orc["mu"].iters
+    assert abs(out["mu"] - orc["mu"].mu) < 1e-12
+    assert relF(out["gmoments"].cpu().numpy(), orc["gmoments"]) < 1e-10
+    assert relF(out["F_host"], orc["F"].vals) < 1e-10
+    assert abs(out["trace_FS"] - N_e) < 1e-6
+
+
+def test_invalid_pattern_and_workspace_errors():
+    rp = torch.tensor([0, 1, 2], dtype=torch.int64, device=DEV)
+    ci = torch.tensor([1, 1], dtype=torch.int32, device=DEV)  # row 0 misses its diagonal
+    with pytest.raises(cg.ChebError) as e:
+        cg.Plan(cg.Bsr(rp, ci), cg.F64)
+    assert e.value.code == 1
+    ci2 = torch.tensor([0, 1, 1], dtype=torch.int32, device=DEV)
+    rp2 = torch.tensor([0, 2, 3], dtype=torch.int64, device=DEV)  # (0,1) present, (1,0) missing
+    with pytest.raises(cg.ChebError) as e:
+        cg.Plan(cg.Bsr(rp2, ci2), cg.F64)
+    assert "symmetric" in str(e.value)
