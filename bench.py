@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark: density-matrix solves/s of the sparse Chebyshev (FOE) method on GB300.
+
+One step = one complete density-matrix solve of a synthetic atom-centred system
+(10,000 atoms x 4 basis functions = 40,000 rows, 10 bohr block cutoff, 4 bohr
+output buffer, kT = 0.005 Ha, N_e = 20,000), from device-resident inputs (atom
+positions, S and H on their block pattern): block patterns, plans, S^-1/2 by
+an FP64 power expansion, H', Lanczos bounds, coefficients and degree, the
+moment pass, the mu bisection, the accumulation pass with 4 simultaneous mu
+(FP32 block products, FP64 accumulators), post-processing and Tr(FS).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cheb|reference]
+N > 1 runs under torchrun: each rank solves its own system (seed = rank), no
+collective on the data path (weak scaling); timing is the max over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "density-matrix solves/s at <=1e-6 vs FP64 plain; masked SpGEMM HBM GB/s"
+UNIT = "solves/s"
+FALLBACK_HBM_GBS = 6800.0
+SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+
+WORKLOADS = {
+    # The mixed-precision density matrix: 10,000 atoms x 4, 10 bohr cutoff.
+    "foe_mixed_40k": dict(n_atoms=10000, r_c=10.0, r_buf=4.0, kT=0.005, N_e=20000.0, tol=1e-7, tol_S=1e-10,
+                          precision="f32", n_mu=4),
+    # The plain FP64 density matrix: 200 atoms x 4, 8 bohr cutoff, kT = 0.01, N_e = 400.
+    "foe_fp64_800": dict(n_atoms=200, r_c=8.0, r_buf=4.0, kT=0.01, N_e=400.0, tol=1e-10, tol_S=1e-10,
+                         precision="f64", n_mu=1),
+}
+DEFAULT_WORKLOAD = "foe_mixed_40k"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# algorithmic accounting of the recursion step
+# --------------------------------------------------------------------------
+
+def count_triples(row_ptr_H, col_idx_H, row_ptr_O, col_idx_O) -> int:
+    """Number of (I,K,J) with (I,K) in P_H, (K,J) in P_out and (I,J) in P_out."""
+    import scipy.sparse as sp
+    n = len(row_ptr_H) - 1
+    A = sp.csr_matrix((np.ones(len(col_idx_H), np.float64), col_idx_H, row_ptr_H), shape=(n, n))
+    B = sp.csr_matrix((np.ones(len(col_idx_O), np.float64), col_idx_O, row_ptr_O), shape=(n, n))
+    return int(round((A @ B).multiply(B).sum()))
+
+
+def step_bytes(nnz_out: int, nnz_H: int, esz: int, n_acc: int, with_G: bool) -> int:
+    """Algorithmic bytes of one recursion step: read T_k, T_{k-1} and H~ once, write
+    T_{k+1}, read+write each FP64 accumulator, read the FP64 functional G."""
+    b = nnz_out * 16 * esz * 3 + nnz_H * 16 * esz + nnz_out * 16 * 8 * 2 * n_acc
+    if with_G:
+        b += nnz_out * 16 * 8
+    return b
+
+
+def measured_hbm_peak() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+            if k in d:
+                return float(d[k]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# --------------------------------------------------------------------------
+# the CUDA arm
+# --------------------------------------------------------------------------
+
+def run_cheb(args, rank: int, world: int, local: int):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_1704_00512_gb300 as cg
+    from paper_1704_00512_gb300 import solve
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = WORKLOADS[args.workload]
+    prec = cg.F32 if cfg["precision"] == "f32" else cg.F64
+    t0 = time.time()
+    sysm = synth.make_system(cfg["n_atoms"], cfg["r_c"], seed=rank)
+    log(f"[rank {rank}] generated {sysm.n_rows} rows, {sysm.nnzb} blocks in {time.time() - t0:.1f}s")
+    pb = solve.problem_from_system(sysm, cfg["r_buf"], dev, prec)
+    kw = dict(kT=cfg["kT"], N_e=cfg["N_e"], tol=cfg["tol"], tol_S=cfg["tol_S"], n_mu=cfg["n_mu"])
+
+    def step(timings=None):
+        pb.build_patterns()
+        return solve.foe(pb, timings=timings, **kw)
+
+    for i in range(args.warmup):
+        tw = time.time()
+        out = step()
+        torch.cuda.synchronize()
+        log(f"[rank {rank}] warmup {i}: {time.time() - tw:.2f}s n_terms={out['n_terms']} mu={out['mu']:.6f} "
+            f"TrFS={out['trace_FS'].item():.6f}")
+    n_terms = out["n_terms"]
+    nnz_out, nnz_H = pb.P_out.nnzb, pb.P_H.nnzb
+    triples = count_triples(pb.P_H.row_ptr.cpu().numpy(), pb.P_H.col_idx.cpu().numpy(),
+                            pb.P_out.row_ptr.cpu().numpy(), pb.P_out.col_idx.cpu().numpy())
+
+    # ---- device-resident timed region
+    clk = ClockSampler(local)
+    pass_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = cg.launch_count()
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        tm = {}
+        out = step(tm)
+        pass_ms.append(tm["events"])
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = cg.launch_count() - l0
+    if world > 1:
+        dist.barrier()
+    t_ms = e0.elapsed_time(e1)
+    p1 = sum(ev[0].elapsed_time(ev[1]) for ev in pass_ms) / args.steps
+    p2 = sum(ev[2].elapsed_time(ev[3]) for ev in pass_ms) / args.steps
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = args.steps * world / (t_ms / 1e3)
+
+    # ---- end-to-end through the same API from pinned host buffers
+    h_xyz = torch.from_numpy(np.ascontiguousarray(sysm.xyz)).pin_memory()
+    h_S = torch.from_numpy(np.ascontiguousarray(sysm.S)).pin_memory()
+    h_H = torch.from_numpy(np.ascontiguousarray(sysm.H)).pin_memory()
+    h_F = torch.empty((nnz_out, 4, 4), dtype=torch.float64).pin_memory()
+    h_mu = torch.empty(1, dtype=torch.float64).pin_memory()
+    h2d = h_xyz.numel() * 8 + h_S.numel() * 8 + h_H.numel() * 8
+    d2h = h_F.numel() * 8 + 8
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(args.steps):
+        pb.xyz.copy_(h_xyz, non_blocking=True)
+        pb.S.vals.copy_(h_S, non_blocking=True)
+        pb.H.vals.copy_(h_H, non_blocking=True)
+        o = step()
+        h_F.copy_(o["F"], non_blocking=True)
+        h_mu.copy_(o["trace_FS"], non_blocking=True)
+    f1.record()
+    torch.cuda.synchronize()
+    te_ms = f0.elapsed_time(f1)
+    if world > 1:
+        tt = torch.tensor([te_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te_ms = float(tt.item())
+    e2e_value = args.steps * world / (te_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (the fused recursion step)
+    esz = 4 if prec == cg.F32 else 8
+    steps_per_pass = n_terms - 2
+    b1 = step_bytes(nnz_out, nnz_H, esz, 0, True)
+    b2 = step_bytes(nnz_out, nnz_H, esz, cfg["n_mu"], False)
+    flops = 2.0 * 64.0 * triples
+    pass_s = (p1 + p2) / 1e3
+    gbs = (b1 + b2) * steps_per_pass / pass_s / 1e9
+    tflops = 2 * flops * steps_per_pass / pass_s / 1e12
+    hbm_peak, hbm_src = measured_hbm_peak()
+    if prec == cg.F32:
+        alu_peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+        alu_note = "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"
+    else:
+        alu_peak = None
+        alu_note = "FP64 peak not derived"
+    hbm_frac = gbs / hbm_peak
+    alu_frac = tflops / alu_peak if alu_peak else None
+    if alu_frac is not None and alu_frac > hbm_frac:
+        roof = {"bound": "alu", "achieved": round(tflops, 3), "peak": round(alu_peak, 3), "unit": "TFLOP/s",
+                "frac": round(alu_frac, 4), "traffic": None, "peak_source": alu_note}
+    else:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(hbm_frac, 4), "traffic": None, "peak_source": f"{hbm_src} copy bandwidth"}
+    roof["kernel"] = "k_step<float,4,16>" if prec == cg.F32 else "k_step<double,2,8>"
+    roof["algorithmic_bytes_per_launch"] = int((b1 + b2) / 2)
+    roof["algorithmic_flops_per_launch"] = flops
+    roof["avg_launch_ms"] = round((p1 + p2) / (2 * steps_per_pass), 5)
+
+    res = {
+        "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == cg.F32 else "f64",
+        "data": "synthetic (seeded atom-centred S/H generator; paper's BigDFT matrices unavailable)",
+        "config": {"workload": args.workload, "atoms_per_gpu": cfg["n_atoms"], "rows": 4 * cfg["n_atoms"],
+                   "r_c": cfg["r_c"], "r_buf": cfg["r_buf"], "kT": cfg["kT"], "N_e": cfg["N_e"],
+                   "fit_tol": cfg["tol"], "n_mu": cfg["n_mu"], "n_terms": n_terms,
+                   "blocks_P_H": nnz_H, "blocks_P_out": nnz_out, "triples": triples,
+                   "products": "fp32" if prec == cg.F32 else "fp64", "accumulators": "fp64",
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush)"},
+        "spgemm_hbm_gbs": round(gbs, 1),
+        "pass_ms": {"moments": round(p1, 2), "accumulate": round(p2, 2)},
+        "roofline": roof,
+        "e2e": {"value": round(e2e_value, 5), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "check": {"trace_FS": float(out["trace_FS"].item()), "mu": out["mu"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(sysm, cfg, n_terms, out["n_S"])
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+# --------------------------------------------------------------------------
+# the CPU oracle: baseline leg and reference arm
+# --------------------------------------------------------------------------
+
+def oracle_sample(sysm, cfg, n_products: int = 1):
+    """Time n_products steps of the oracle's masked recursion on this system."""
+    from oracle import ref
+    S = ref.Bsr(sysm.row_ptr, sysm.col_idx, sysm.S)
+    H = ref.Bsr(sysm.row_ptr, sysm.col_idx, sysm.H)
+    rp, ci = ref.pattern(sysm.xyz, sysm.L, cfg["r_c"] + cfg["r_buf"])
+    P_out = ref.Bsr(rp, ci, None)
+    Ht = ref.scale(H, -10.0, 10.0)
+    coeffs = np.ones((cfg["n_mu"], n_products + 2))
+    t0 = time.perf_counter()
+    ref.chebyshev_expand(Ht, P_out, coeffs, G=ref.identity(P_out) if cfg["n_mu"] == 1 else None)
+    dt = time.perf_counter() - t0
+    del S
+    return dt / n_products, len(ci)
+
+
+def solve_step_equivalents(n_terms: int, n_S: int, nnz_out: int, nnz_H: int) -> float:
+    """Recursion-step equivalents of one solve: two passes of n_terms-2 steps, the
+    S^-1/2 expansion, and six P_out x P_out products (orthogonalisation, the trace
+    functional, post-processing), each nnz_out/nnz_H times a step."""
+    return 2 * (n_terms - 2) + (n_S - 2) + 6 * nnz_out / nnz_H
+
+
+def cpu_baseline(sysm, cfg, n_terms, n_S) -> dict:
+    t_step, nnz_out = oracle_sample(sysm, cfg, 1)
+    eq = solve_step_equivalents(n_terms, n_S, nnz_out, sysm.nnzb)
+    return {"value": 1.0 / (t_step * eq), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"1 FP64 recursion step of the same system timed ({t_step:.2f}s), scaled by "
+                      f"{eq:.0f} step-equivalents per solve"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    import synth
+    cfg = WORKLOADS[args.workload]
+    sysm = synth.make_system(cfg["n_atoms"], cfg["r_c"], seed=0)
+    # term counts of the solve come from the oracle's own degree rule on a
+    # representative interval; the sample times one recursion step per bench step
+    from oracle import ref
+    n_terms = ref.choose_degree(ref.Func(ref.KIND_FERMI, mu=0.0, kT=cfg["kT"]), -8.6, 8.6, cfg["tol"], 16384)
+    n_S = ref.choose_degree(ref.Func(ref.KIND_POWER, a=-0.5), 0.03, 3.1, cfg["tol_S"], 512, rel=True)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t_step, nnz_out = oracle_sample(sysm, cfg, 1)
+        if i >= args.warmup:
+            times.append(t_step)
+    eq = solve_step_equivalents(n_terms, n_S, nnz_out, sysm.nnzb)
+    t_solve = statistics.mean(times) * eq
+    value = 1.0 / t_solve
+    res = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "atoms_per_gpu": cfg["n_atoms"], "rows": 4 * cfg["n_atoms"],
+                      "n_terms": n_terms, "n_S": n_S},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": f"per bench step one FP64 oracle recursion step of the same system, "
+                                      f"scaled by {eq:.0f} step-equivalents per solve"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cheb", "reference"], default="cheb")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("note: fewer than 3 warm-up steps")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_cheb(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -83,6 +83,10 @@ typedef struct cheb_func {
 /* Message of the last failure in this thread ("" if none).  Never NULL. */
 const char *cheb_last_error(void);
 
+/* Number of kernel launches this process has made through the library (all
+ * threads, all devices).  For accounting only; never resets. */
+uint64_t cheb_launch_count(void);
+
 /* ---------------------------------------------------------------------------
  * Sparsity patterns.  Sec. "Sparsity and truncation": the library works on a
  * fixed pattern; the output pattern is a larger "buffer" pattern.  Both are
@@ -111,10 +115,14 @@ int cheb_pattern_build(const double *xyz, int64_t n_atoms, double box_L, double 
  * together (columns are independent under Eq. 3, Sec. "Expansion in Chebyshev
  * polynomials").  precision (CHEB_F64 / CHEB_F32) selects the panel width.
  *
+ * The step kernel comes in several tile shapes per precision (panel width,
+ * warps per block, blocks per SM); cheb_tile_count / cheb_tile_info list them.
+ *
  * cheb_plan_create (host-returning): reads P_out's row_ptr/col_idx (device)
  * to the host, checks symmetry, sortedness and diagonal blocks
- * (CHEB_ERR_INVALID otherwise), groups columns, and returns a host-allocated
- * plan and the device workspace it needs in *plan_ws_bytes.
+ * (CHEB_ERR_INVALID otherwise), groups columns into panels for tile shape
+ * `tile` (-1 = the default shape of the precision), and returns a
+ * host-allocated plan and the device workspace it needs in *plan_ws_bytes.
  * cheb_plan_bind copies the plan tables into caller device memory plan_ws
  * (>= plan_ws_bytes, 256-byte aligned); the plan then refers to that memory,
  * which must stay valid until cheb_plan_destroy.  P_out's row_ptr/col_idx
@@ -123,7 +131,10 @@ int cheb_pattern_build(const double *xyz, int64_t n_atoms, double box_L, double 
  */
 typedef struct cheb_plan cheb_plan;
 
-int cheb_plan_create(const cheb_bsr *P_out, int32_t precision, cheb_plan **plan,
+int cheb_tile_count(int32_t precision);
+int cheb_tile_info(int32_t precision, int32_t tile, int32_t *panel_width, int32_t *warps,
+                   int32_t *blocks_per_sm);
+int cheb_plan_create(const cheb_bsr *P_out, int32_t precision, int32_t tile, cheb_plan **plan,
                      size_t *plan_ws_bytes, void *stream);
 int cheb_plan_bind(cheb_plan *plan, void *plan_ws, size_t plan_ws_bytes, void *stream);
 int cheb_plan_info(const cheb_plan *plan, int64_t *n_panels, int32_t *panel_width,

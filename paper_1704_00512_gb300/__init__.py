@@ -6,6 +6,6 @@ the C entry points) plus the solve sequences (``solve``) that chain those calls.
 """
 from ._lib import (  # noqa: F401
     BF16, ERFC, F32, F64, FERMI, INTERVAL, PENALTY, POWER, Bsr, ChebError, Plan, bounds, coeffs,
-    decode_mu_result, expand, expand_workspace_size, load, masked_product, mu_search, newton_schulz,
-    pattern_build, penalty_trace, restrict, scale, trace, transpose,
+    decode_mu_result, expand, expand_workspace_size, launch_count, load, masked_product, mu_search, newton_schulz,
+    pattern_build, penalty_trace, restrict, scale, tile_shapes, trace, transpose,
 )

@@ -25,7 +25,7 @@ FERMI, ERFC, POWER, INTERVAL, PENALTY = 0, 1, 2, 3, 4
 
 # Every symbol declared in include/cheb.h.
 EXPORTS = [
-    "cheb_last_error", "cheb_pattern_build", "cheb_plan_create", "cheb_plan_bind", "cheb_plan_info",
+    "cheb_last_error", "cheb_launch_count", "cheb_pattern_build", "cheb_tile_count", "cheb_tile_info", "cheb_plan_create", "cheb_plan_bind", "cheb_plan_info",
     "cheb_plan_destroy", "cheb_scale", "cheb_bounds_workspace_size", "cheb_bounds",
     "cheb_coeffs_workspace_size", "cheb_coeffs", "cheb_expand_workspace_size", "cheb_expand",
     "cheb_masked_product", "cheb_transpose", "cheb_restrict", "cheb_trace_workspace_size", "cheb_trace",
@@ -66,8 +66,11 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
     P = ctypes.POINTER
     sig = {
         "cheb_last_error": ([], ctypes.c_char_p),
+        "cheb_launch_count": ([], ctypes.c_uint64),
         "cheb_pattern_build": ([p, i64, dbl, dbl, p, p, P(i64), p], i32),
-        "cheb_plan_create": ([P(CBsr), i32, P(p), P(sz), p], i32),
+        "cheb_tile_count": ([i32], i32),
+        "cheb_tile_info": ([i32, i32, P(i32), P(i32), P(i32)], i32),
+        "cheb_plan_create": ([P(CBsr), i32, i32, P(p), P(sz), p], i32),
         "cheb_plan_bind": ([p, p, sz, p], i32),
         "cheb_plan_info": ([p, P(i64), P(i32), P(i32)], i32),
         "cheb_plan_destroy": ([p], i32),
@@ -152,6 +155,22 @@ class Bsr:
                     _ptr(self.vals) if self.vals is not None else None, dt)
 
 
+def tile_shapes(precision: int) -> list[tuple[int, int, int]]:
+    """cheb_tile_count / cheb_tile_info: (panel width, warps, blocks per SM) per tile index."""
+    lib = load()
+    out = []
+    for t in range(lib.cheb_tile_count(precision)):
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.cheb_tile_info(precision, t, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        out.append((a.value, b.value, c.value))
+    return out
+
+
+def launch_count() -> int:
+    """cheb_launch_count: kernel launches made through the library so far."""
+    return int(load().cheb_launch_count())
+
+
 def pattern_build(xyz: torch.Tensor, box_L: float, r_cut: float, stream=None) -> tuple[torch.Tensor, torch.Tensor]:
     """cheb_pattern_build (both calls)."""
     lib = load()
@@ -168,15 +187,16 @@ def pattern_build(xyz: torch.Tensor, box_L: float, r_cut: float, stream=None) ->
 class Plan:
     """cheb_plan_create + cheb_plan_bind; keeps the pattern and workspace alive."""
 
-    def __init__(self, P_out: Bsr, precision: int = F64, stream=None):
+    def __init__(self, P_out: Bsr, precision: int = F64, tile: int = -1, stream=None):
         lib = load()
         self.P_out = P_out
         self.precision = precision
+        self.tile = tile
         h = ctypes.c_void_p()
         nbytes = ctypes.c_size_t(0)
         s = _stream(stream)
         cb = P_out.c()
-        _check(lib.cheb_plan_create(ctypes.byref(cb), precision, ctypes.byref(h), ctypes.byref(nbytes), s))
+        _check(lib.cheb_plan_create(ctypes.byref(cb), precision, tile, ctypes.byref(h), ctypes.byref(nbytes), s))
         self.handle = h
         self._ws = _ws(nbytes.value, P_out.row_ptr.device)
         _check(lib.cheb_plan_bind(h, ctypes.c_void_p(_aligned(self._ws)), nbytes.value, s))

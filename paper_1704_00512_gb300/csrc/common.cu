@@ -1,5 +1,7 @@
 // Error state and the small elementwise kernels: scale (Eq. 2), transpose,
 // restrict, trace (Tr(KS) = N, Sec. "Fermi Operator Expansion").
+#include <atomic>
+
 #include "common.cuh"
 #include "plan.cuh"
 
@@ -20,7 +22,10 @@ int fail(int code, const char *fmt, ...) {
     return code;
 }
 
-int check_launch(const char *what) {
+static std::atomic<unsigned long long> g_launches{0};
+
+int check_launch(const char *what, int n_launches) {
+    g_launches.fetch_add((unsigned long long)n_launches, std::memory_order_relaxed);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(CHEB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
     return CHEB_OK;
@@ -99,6 +104,8 @@ constexpr int TRACE_GRID = 304;
 using namespace cheb;
 
 extern "C" const char *cheb_last_error(void) { return last_error().c_str(); }
+
+extern "C" uint64_t cheb_launch_count(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
 static int check_bsr(const cheb_bsr *M, const char *name, bool need_vals) {
     if (!M) return fail(CHEB_ERR_INVALID, "%s is NULL", name);

@@ -22,8 +22,9 @@ int fail(int code, const char *fmt, ...);
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// Checks the launch that just happened on this thread.
-int check_launch(const char *what);
+// Checks the launch(es) that just happened on this thread and counts them
+// (cheb_launch_count).
+int check_launch(const char *what, int n_launches = 1);
 
 #define CHEB_CUDA(call)                                                                  \
     do {                                                                                 \

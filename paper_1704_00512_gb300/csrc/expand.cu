@@ -122,15 +122,20 @@ __device__ __forceinline__ int block_excl_scan(int v, int *wsum, int *total) {
     return excl;
 }
 
+template <int NV>
+struct Moments {
+    double v[NV];    // this thread's partial sums
+    double *dst[NV];  // device scalars receiving the totals (NULL = not wanted)
+};
+
 // Deterministic sum of the per-block partials by the last block to finish.
 template <int NT, int NV>
-__device__ __forceinline__ void finish_moments(double *part, int32_t *counter, double (&v)[NV],
-                                               double *const (&dst)[NV], double *red) {
+__device__ __forceinline__ void finish_moments(double *part, int32_t *counter, const Moments<NV> m, double *red) {
     __shared__ int s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-        double w = warp_sum(v[i]);
+        double w = warp_sum(m.v[i]);
         if (lane == 0) red[warp * NV + i] = w;
     }
     __syncthreads();
@@ -166,31 +171,64 @@ __device__ __forceinline__ void finish_moments(double *part, int32_t *counter, d
         for (int i = 0; i < NV; ++i) {
             double s = 0.0;
             for (int w = 0; w < NT / 32; ++w) s += red[w * NV + i];
-            if (dst[i]) *dst[i] = s;
+            if (m.dst[i]) *m.dst[i] = s;
         }
         *counter = 0;
         __threadfence();
     }
 }
 
-template <typename T, int P, int NW>
-__global__ void __launch_bounds__(NW * 32, 1) k_step(const StepArgs<T> a) {
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    static __device__ __forceinline__ void ld(float (&v)[4], const float *p) {
+        float4 a = *reinterpret_cast<const float4 *>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    static __device__ __forceinline__ void ldg(float (&v)[4], const float *p) {
+        float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float (&v)[4]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <>
+struct Vec4<double> {
+    static __device__ __forceinline__ void ld(double (&v)[4], const double *p) {
+        double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void ldg(double (&v)[4], const double *p) {
+        double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p + 2));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void st(double *p, const double (&v)[4]) {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
+    }
+};
+
+template <typename T, int P, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int wsum[32];
-    __shared__ int s_nu;
     constexpr int NT = NW * 32;
     constexpr int KG = 32 / P;                  // K-groups per warp
-    constexpr int EPL = KG >= 16 ? 1 : 16 / KG;  // epilogue elements per lane
-    const StepLayout lay = step_layout(a.nw, a.ucap, P, sizeof(T));
+    constexpr int NU = 32 / KG;                 // staged entries per K-group per 32-chunk
+    constexpr int EPL = KG >= 16 ? 1 : 16 / KG;  // raw-store elements per lane
+    const StepLayout lay = step_layout(a.nw, a.ucap, P, sizeof(T), NW);
     uint2 *bits = reinterpret_cast<uint2 *>(smem + lay.off_bits);
     int32_t *ulist = reinterpret_cast<int32_t *>(smem + lay.off_ulist);
     int16_t *pos = reinterpret_cast<int16_t *>(smem + lay.off_pos);
+    int2 *wlist = reinterpret_cast<int2 *>(smem + lay.off_wl);
     T *X = reinterpret_cast<T *>(smem + lay.off_x);
     double *red = reinterpret_cast<double *>(smem + lay.off_red);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j0 = a.panels[2 * blockIdx.x], ncols = a.panels[2 * blockIdx.x + 1];
 
-    // 1. bitmap of the rows present in the panel's columns
+    // 1. bitmap of the rows present in the panel's columns, ranks, union list
     for (int64_t w = tid; w < a.nw; w += NT) bits[w] = make_uint2(0u, 0u);
     __syncthreads();
     for (int q = 0; q < ncols; ++q) {
@@ -207,7 +245,6 @@ __global__ void __launch_bounds__(NW * 32, 1) k_step(const StepArgs<T> a) {
     for (int64_t w = wb; w < we; ++w) cnt += __popc(bits[w].x);
     int total;
     int run = block_excl_scan<NW>(cnt, wsum, &total);
-    if (tid == 0) s_nu = total;
     for (int64_t w = wb; w < we; ++w) {
         unsigned m = bits[w].x;
         bits[w].y = (unsigned)run;
@@ -219,7 +256,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_step(const StepArgs<T> a) {
     }
     const int nu = total;
     if (nu > a.ucap) return;  // cannot happen for a plan-built launch (uniform exit)
-    // 2. gather the panel's columns of T_k
+    // 2. gather the panel's columns of T_k into X[slot][4][4P] (zero elsewhere)
     {
         uint4 *x4 = reinterpret_cast<uint4 *>(X);
         const int64_t n4 = (int64_t)nu * BB * P * sizeof(T) / 16;
@@ -245,67 +282,158 @@ __global__ void __launch_bounds__(NW * 32, 1) k_step(const StepArgs<T> a) {
     }
     __syncthreads();
 
-    // 3.-4. rows of the union: masked block products, reduction, epilogue
-    const int q = lane % P, kg = lane / P;
-    double coefv[MAX_F];
+    // 3. union rows: masked block products M~_I. X for the panel's columns.
+    // The row's blocks are ranked 32 at a time (one block per lane); those
+    // whose column K is in the union are appended to the warp's staging ring.
+    // Whenever 32 entries are staged, each K-group takes NU of them, issues
+    // their loads back to back and then does the FMAs, so every batch but the
+    // row's last is full and the loads of a batch are in flight together.
+    {
+        const int q = lane % P, kg = lane / P;
+        const unsigned lt = (1u << lane) - 1u;
+        int2 *wl = wlist + warp * 64;
+        auto batch = [&](T(&acc)[16], int navail) {
+            int2 en[NU];
+            T h[NU][16];
 #pragma unroll
-    for (int f = 0; f < MAX_F; ++f) coefv[f] = f < a.nf ? a.coef[(int64_t)f * a.coef_stride + a.term] : 0.0;
-    double tpart = 0.0, gpart = 0.0;
-    for (int s = warp; s < nu; s += NW) {
-        const int I = ulist[s];
-        T acc[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) acc[i] = T(0);
-        const int64_t a1 = a.Lrp[I + 1];
-        for (int64_t ai = a.Lrp[I] + kg; ai < a1; ai += KG) {
-            const int K = a.Lci[ai];
-            const int s2 = rank_of(bits, K);
-            if (s2 < 0) continue;
-            T h[16];
-            load16<T>(h, a.Lv + ai * BB);
-            const T *xs = X + (int64_t)s2 * BB * P + 4 * q;
-            const int sw = s2 & 1;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                T x[4];
-                lds4<T>(x, xs + (m ^ sw) * 4 * P);
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[4 * r + c] = fma(h[4 * r + m], x[c], acc[4 * r + c]);
+            for (int u = 0; u < NU; ++u) {
+                const int e = u * KG + kg;
+                en[u] = e < navail ? wl[e] : make_int2(-1, 0);
+                if (en[u].x >= 0) load16<T>(h[u], a.Lv + (int64_t)en[u].x * BB);
             }
-        }
 #pragma unroll
-        for (int o = P; o < 32; o <<= 1)
+            for (int u = 0; u < NU; ++u) {
+                if (en[u].x < 0) continue;
+                const T *xs = X + en[u].y * (BB * P) + 4 * q;
+                const int sw = en[u].y & 1;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
-        if (q < ncols && kg * EPL < 16) {
-            const int e = pos[s * P + q];
-            if (e >= 0) {
-                const int J = j0 + q;
-                const int64_t slot = (int64_t)a.tperm[a.rp[J] + e] * BB;
-                const bool diag = I == J;
+                for (int m = 0; m < 4; ++m) {
+                    T x[4];
+                    lds4<T>(x, xs + (m ^ sw) * 4 * P);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    if (i / EPL != kg) continue;
-                    const int64_t idx = slot + i;
-                    T y = a.alpha * acc[i];
-                    if (a.Rm) y = y + a.beta * a.Rm[idx];
-                    a.C[idx] = y;
-                    const double yd = (double)y;
+                    for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int f = 0; f < MAX_F; ++f)
-                        if (f < a.nf) a.acc[f][idx] += coefv[f] * yd;
-                    if (a.G) gpart += a.G[idx] * yd;
-                    if (diag && (i % 5) == 0) tpart += yd;
+                        for (int c = 0; c < 4; ++c) acc[4 * r + c] = fma(h[u][4 * r + m], x[c], acc[4 * r + c]);
+                }
+            }
+        };
+        for (int s = warp; s < nu; s += NW) {
+            const int I = ulist[s];
+            const int64_t a0 = a.Lrp[I], a1 = a.Lrp[I + 1];
+            T acc[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] = T(0);
+            int pending = 0;
+            int64_t base = a0;
+            int Knext = (a0 + lane < a1) ? a.Lci[a0 + lane] : -1;
+            while (true) {
+                if (base < a1) {
+                    const int K = Knext;
+                    Knext = (base + 32 + lane < a1) ? a.Lci[base + 32 + lane] : -1;
+                    const int s2 = K >= 0 ? rank_of(bits, K) : -1;
+                    const unsigned vm = __ballot_sync(0xffffffffu, s2 >= 0);
+                    if (s2 >= 0) wl[pending + __popc(vm & lt)] = make_int2((int)(base + lane), s2);
+                    pending += __popc(vm);
+                    base += 32;
+                    __syncwarp();
+                }
+                const bool raw_done = base >= a1;
+                if (pending >= 32 || (raw_done && pending > 0)) {
+                    const int n = pending < 32 ? pending : 32;
+                    batch(acc, n);
+                    __syncwarp();
+                    const int rest = pending - n;
+                    const int2 keep = lane < rest ? wl[n + lane] : make_int2(0, 0);
+                    __syncwarp();
+                    if (lane < rest) wl[lane] = keep;
+                    pending = rest;
+                    __syncwarp();
+                }
+                if (raw_done && pending == 0) break;
+            }
+#pragma unroll
+            for (int o = P; o < 32; o <<= 1)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+            // raw product into the output slot; the epilogue below finishes it
+            if (q < ncols && kg * EPL < 16) {
+                const int e = pos[s * P + q];
+                if (e >= 0) {
+                    const int64_t slot = (int64_t)a.tperm[a.rp[j0 + q] + e] * BB;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (i / EPL == kg) a.C[slot + i] = acc[i];
                 }
             }
         }
     }
+    __syncthreads();
+
+    // 4. epilogue over the panel's output blocks, one block row (4 elements) per
+    // thread in column order: T_{k+1} = alpha * (M~ T_k) + beta * T_{k-1},
+    // accumulators, Tr T_{k+1} and <T_{k+1}, G>.
+    double coefv[MAX_F];
+#pragma unroll
+    for (int f = 0; f < MAX_F; ++f) coefv[f] = f < a.nf ? a.coef[(int64_t)f * a.coef_stride + a.term] : 0.0;
+    // cumulative block counts of the panel's columns (indexed by constants only)
+    int cum[5];
+    cum[0] = 0;
+    int nblk = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        cum[q + 1] = cum[q] + (q < ncols ? (int)(a.rp[j0 + q + 1] - a.rp[j0 + q]) : 0);
+        if (q < ncols) nblk = cum[q + 1];
+    }
+    double tpart = 0.0, gpart = 0.0;
+    for (int t = tid; t < nblk * 4; t += NT) {
+        const int b = t >> 2, r = t & 3;
+        int q = 0, base = 0;
+#pragma unroll
+        for (int qq = 1; qq < 4; ++qq)
+            if (qq < ncols && b >= cum[qq]) {
+                q = qq;
+                base = cum[qq];
+            }
+        const int J = j0 + q;
+        const int64_t p = a.rp[J] + (b - base);
+        const int K = a.ci[p];
+        const int64_t idx = (int64_t)a.tperm[p] * BB + 4 * r;
+        T y[4];
+        Vec4<T>::ld(y, a.C + idx);
+        if (a.Rm) {
+            T m4[4];
+            Vec4<T>::ldg(m4, a.Rm + idx);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) y[c] = a.alpha * y[c] + a.beta * m4[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) y[c] = a.alpha * y[c];
+        }
+        Vec4<T>::st(a.C + idx, y);
+        double yd[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) yd[c] = (double)y[c];
+#pragma unroll
+        for (int f = 0; f < MAX_F; ++f) {
+            if (f < a.nf) {
+                double v[4];
+                Vec4<double>::ld(v, a.acc[f] + idx);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[c] += coefv[f] * yd[c];
+                Vec4<double>::st(a.acc[f] + idx, v);
+            }
+        }
+        if (a.G) {
+            double gv[4];
+            Vec4<double>::ldg(gv, a.G + idx);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) gpart += gv[c] * yd[c];
+        }
+        if (K == J) tpart += yd[r];
+    }
     if (a.mom || a.gmom) {
-        double v[2] = {tpart, gpart};
-        double *const dst[2] = {a.mom, a.gmom};
-        finish_moments<NT, 2>(a.part, a.counter, v, dst, red);
+        Moments<2> mm{{tpart, gpart}, {a.mom, a.gmom}};
+        finish_moments<NT, 2>(a.part, a.counter, mm, red);
     }
 }
 
@@ -353,9 +481,8 @@ __global__ void __launch_bounds__(NT) k_init(const int64_t *rp, const int32_t *c
             }
         }
     }
-    double v[4] = {t0, t1, g0, g1};
-    double *const dst[4] = {mom, mom ? mom + 1 : nullptr, gmom, gmom ? gmom + 1 : nullptr};
-    finish_moments<NT, 4>(a.part, a.counter, v, dst, red);
+    Moments<4> mm{{t0, t1, g0, g1}, {mom, mom ? mom + 1 : nullptr, gmom, gmom ? gmom + 1 : nullptr}};
+    finish_moments<NT, 4>(a.part, a.counter, mm, red);
 }
 
 __global__ void k_to_f32(const double *in, float *out, int64_t n) {
@@ -363,10 +490,10 @@ __global__ void k_to_f32(const double *in, float *out, int64_t n) {
     if (i < n) out[i] = (float)in[i];
 }
 
-template <typename T, int P, int NW>
+template <typename T, int P, int NW, int MINB>
 int launch_step(const cheb_plan *plan, const StepArgs<T> &a, cudaStream_t s) {
-    const StepLayout lay = step_layout(a.nw, a.ucap, P, sizeof(T));
-    auto fn = k_step<T, P, NW>;
+    const StepLayout lay = step_layout(a.nw, a.ucap, P, sizeof(T), NW);
+    auto fn = k_step<T, P, NW, MINB>;
     CHEB_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
     fn<<<(unsigned)plan->n_panels, NW * 32, lay.total, s>>>(a);
     return check_launch("k_step");
@@ -387,18 +514,36 @@ StepArgs<T> base_args(const cheb_plan *plan, const cheb_bsr *L, const T *Lv) {
     return a;
 }
 
-constexpr int NW_F64 = 8, NW_F32 = 16;
-
 template <typename T>
 int run_step(const cheb_plan *plan, const StepArgs<T> &a, cudaStream_t s);
+#define CHEB_TILE_CASE(T, TABLE, i) \
+    case i: return launch_step<T, TABLE[i].P, TABLE[i].NW, TABLE[i].MINB>(plan, a, s);
 template <>
 int run_step<double>(const cheb_plan *plan, const StepArgs<double> &a, cudaStream_t s) {
-    return launch_step<double, 2, NW_F64>(plan, a, s);
+    static_assert(N_TILES_F64 == 5, "tile table size");
+    switch (plan->tile) {
+        CHEB_TILE_CASE(double, TILES_F64, 0)
+        CHEB_TILE_CASE(double, TILES_F64, 1)
+        CHEB_TILE_CASE(double, TILES_F64, 2)
+        CHEB_TILE_CASE(double, TILES_F64, 3)
+        CHEB_TILE_CASE(double, TILES_F64, 4)
+        default: return fail(CHEB_ERR_INVALID, "bad FP64 tile %d", plan->tile);
+    }
 }
 template <>
 int run_step<float>(const cheb_plan *plan, const StepArgs<float> &a, cudaStream_t s) {
-    return launch_step<float, 4, NW_F32>(plan, a, s);
+    static_assert(N_TILES_F32 == 6, "tile table size");
+    switch (plan->tile) {
+        CHEB_TILE_CASE(float, TILES_F32, 0)
+        CHEB_TILE_CASE(float, TILES_F32, 1)
+        CHEB_TILE_CASE(float, TILES_F32, 2)
+        CHEB_TILE_CASE(float, TILES_F32, 3)
+        CHEB_TILE_CASE(float, TILES_F32, 4)
+        CHEB_TILE_CASE(float, TILES_F32, 5)
+        default: return fail(CHEB_ERR_INVALID, "bad FP32 tile %d", plan->tile);
+    }
 }
+#undef CHEB_TILE_CASE
 
 size_t expand_ws(const cheb_plan *plan, int64_t nnzL, int precision) {
     const size_t esz = precision == CHEB_F64 ? 8 : 4;

@@ -245,7 +245,7 @@ extern "C" int cheb_bounds(const cheb_bsr *M, int32_t k, const double *v0, doubl
     k_lz_vec<<<LZ_GRID, LZ_NT, 0, s>>>(0, n, w, v, vm, st, 0);
     k_lz_finish<<<1, LZ_NT, 0, s>>>(st, 0, 0);
     k_lz_next<<<LZ_GRID, LZ_NT, 0, s>>>(0, n, w, v, vm, st, 0);
-    CHEB_TRY(check_launch("lanczos start"));
+    CHEB_TRY(check_launch("lanczos start", 3));
     const unsigned sg = (unsigned)((M->nbr * 32 + 255) / 256);
     for (int j = 0; j < k; ++j) {
         k_spmv<<<sg, 256, 0, s>>>(M->row_ptr, M->col_idx, (const double *)M->vals, M->nbr, v, w, st, j);
@@ -254,7 +254,7 @@ extern "C" int cheb_bounds(const cheb_bsr *M, int32_t k, const double *v0, doubl
         k_lz_vec<<<LZ_GRID, LZ_NT, 0, s>>>(2, n, w, v, vm, st, j);
         k_lz_finish<<<1, LZ_NT, 0, s>>>(st, 2, j);
         k_lz_next<<<LZ_GRID, LZ_NT, 0, s>>>(1, n, w, v, vm, st, j);
-        CHEB_TRY(check_launch("lanczos step"));
+        CHEB_TRY(check_launch("lanczos step", 6));
     }
     k_tridiag<<<1, 32, 0, s>>>(st, margin_frac, scratch);
     CHEB_TRY(check_launch("k_tridiag"));

@@ -15,18 +15,34 @@
 
 using namespace cheb;
 
-static int union_capacity(int64_t nbr, int P, int esz) {
+static int union_capacity(int64_t nbr, int P, int esz, int nwarps, size_t budget) {
     int64_t nw = (nbr + 31) / 32;
-    // largest ucap with step_layout(nw, ucap, P, esz).total <= budget
+    // largest ucap with step_layout(nw, ucap, P, esz, nwarps).total <= budget
     int lo = 0, hi = 1 << 16;
     while (lo < hi) {
         int mid = (lo + hi + 1) / 2;
-        if (step_layout(nw, mid, P, esz).total <= (size_t)CHEB_MAX_DYN_SMEM) lo = mid; else hi = mid - 1;
+        if (step_layout(nw, mid, P, esz, nwarps).total <= budget) lo = mid; else hi = mid - 1;
     }
     return std::min(lo, 32767);
 }
 
-extern "C" int cheb_plan_create(const cheb_bsr *P_out, int32_t precision, cheb_plan **out,
+extern "C" int cheb_tile_count(int32_t precision) {
+    if (precision != CHEB_F64 && precision != CHEB_F32) return 0;
+    return n_tiles(precision);
+}
+
+extern "C" int cheb_tile_info(int32_t precision, int32_t tile, int32_t *panel_width, int32_t *warps,
+                              int32_t *blocks_per_sm) {
+    if ((precision != CHEB_F64 && precision != CHEB_F32) || tile < 0 || tile >= n_tiles(precision))
+        return fail(CHEB_ERR_INVALID, "cheb_tile_info: no tile %d for precision %d", tile, precision);
+    const TileCfg c = tile_cfg(precision, tile);
+    if (panel_width) *panel_width = c.P;
+    if (warps) *warps = c.NW;
+    if (blocks_per_sm) *blocks_per_sm = c.MINB;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_create(const cheb_bsr *P_out, int32_t precision, int32_t tile, cheb_plan **out,
                                 size_t *plan_ws_bytes, void *stream) {
     if (!out || !plan_ws_bytes) return fail(CHEB_ERR_INVALID, "cheb_plan_create: NULL output");
     *out = nullptr;
@@ -35,6 +51,8 @@ extern "C" int cheb_plan_create(const cheb_bsr *P_out, int32_t precision, cheb_p
     if (precision != CHEB_F64 && precision != CHEB_F32)
         return fail(CHEB_ERR_INVALID, "cheb_plan_create: precision must be CHEB_F64 or CHEB_F32");
     if (P_out->nnzb >= (int64_t)INT32_MAX) return fail(CHEB_ERR_INVALID, "cheb_plan_create: too many blocks");
+    if (tile < 0) tile = 0;
+    if (tile >= n_tiles(precision)) return fail(CHEB_ERR_INVALID, "cheb_plan_create: no tile %d", tile);
     const int64_t nbr = P_out->nbr, nnzb = P_out->nnzb;
     std::vector<int64_t> rp(nbr + 1);
     std::vector<int32_t> ci(nnzb);
@@ -73,10 +91,14 @@ extern "C" int cheb_plan_create(const cheb_bsr *P_out, int32_t precision, cheb_p
             plan->h_tperm[p] = (int32_t)(it - ci.begin());
         }
     }
-    const int P = panel_width_for(precision);
+    const TileCfg cfg = tile_cfg(precision, tile);
+    const int P = cfg.P;
     const int esz = precision == CHEB_F64 ? 8 : 4;
+    plan->tile = tile;
     plan->P = P;
-    plan->ucap = union_capacity(nbr, P, esz);
+    plan->NW = cfg.NW;
+    plan->minb = cfg.MINB;
+    plan->ucap = union_capacity(nbr, P, esz, cfg.NW, smem_budget(cfg.MINB));
     // greedy panels; stamp[K] = last panel that counted row K
     std::vector<int32_t> stamp(nbr, -1);
     int64_t j = 0, panel = 0;

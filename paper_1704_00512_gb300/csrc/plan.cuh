@@ -14,7 +14,10 @@ struct cheb_plan {
     const int64_t *rp = nullptr;  // device, caller-owned pattern of P_out
     const int32_t *ci = nullptr;
     int32_t precision = CHEB_F64;
+    int32_t tile = 0;       // index into the tile table of this precision
     int32_t P = 1;          // panel width (block columns advanced by one thread block)
+    int32_t NW = 8;         // warps per thread block
+    int32_t minb = 1;       // thread blocks per SM the shared-memory budget allows
     int64_t n_panels = 0;
     int32_t max_union = 0;  // largest union of row lists over a panel
     int32_t ucap = 0;       // union rows that fit in shared memory
@@ -31,12 +34,12 @@ struct cheb_plan {
 namespace cheb {
 
 // Shared-memory layout of the step kernel for a panel of width P over a union of
-// ucap rows, element size esz, nw bitmap words.
+// ucap rows, element size esz, nw bitmap words, nwarps warps.
 struct StepLayout {
-    size_t off_bits, off_ulist, off_pos, off_x, off_red, total;
+    size_t off_bits, off_ulist, off_pos, off_wl, off_x, off_red, total;
 };
 
-__host__ __device__ inline StepLayout step_layout(int64_t nw, int64_t ucap, int P, int esz) {
+__host__ __device__ inline StepLayout step_layout(int64_t nw, int64_t ucap, int P, int esz, int nwarps) {
     StepLayout L;
     size_t o = 0;
     L.off_bits = o;
@@ -48,15 +51,36 @@ __host__ __device__ inline StepLayout step_layout(int64_t nw, int64_t ucap, int 
     L.off_pos = o;
     o += (size_t)ucap * P * 2;  // int16 position of the row within each panel column
     o = (o + 15) / 16 * 16;
+    L.off_wl = o;
+    o += (size_t)nwarps * 64 * 8;  // per-warp ring of staged (block index, union slot) pairs
+    o = (o + 15) / 16 * 16;
     L.off_x = o;
     o += (size_t)ucap * BB * P * esz;  // the gathered panel of T_k
     o = (o + 15) / 16 * 16;
     L.off_red = o;
-    o += 64 * 8;  // per-warp moment partials (<= 32 warps x 2)
+    o += 128 * 8;  // per-warp moment partials (<= 32 warps x 4)
     L.total = o;
     return L;
 }
 
-inline int panel_width_for(int precision) { return precision == CHEB_F64 ? 2 : 4; }
+// Tile shapes of the step kernel: panel width P, warps per block NW, blocks per
+// SM MINB (the shared-memory budget of a block is the SM's share for MINB).
+struct TileCfg {
+    int P, NW, MINB;
+};
+constexpr TileCfg TILES_F32[] = {{4, 16, 1}, {4, 8, 1}, {2, 8, 2}, {2, 8, 3}, {2, 16, 1}, {1, 8, 3}};
+constexpr TileCfg TILES_F64[] = {{2, 8, 1}, {1, 8, 2}, {2, 4, 2}, {1, 4, 3}, {2, 16, 1}};
+constexpr int N_TILES_F32 = sizeof(TILES_F32) / sizeof(TileCfg);
+constexpr int N_TILES_F64 = sizeof(TILES_F64) / sizeof(TileCfg);
+inline int n_tiles(int precision) { return precision == CHEB_F64 ? N_TILES_F64 : N_TILES_F32; }
+inline TileCfg tile_cfg(int precision, int tile) {
+    return precision == CHEB_F64 ? TILES_F64[tile] : TILES_F32[tile];
+}
+// Dynamic shared memory one block may use when MINB blocks share an SM
+// (228 KB per SM, 1 KB reserved per block, a little static shared memory).
+inline size_t smem_budget(int minb) {
+    size_t per = 233472 / (size_t)minb - 1024 - 512;
+    return per < (size_t)CHEB_MAX_DYN_SMEM ? per : (size_t)CHEB_MAX_DYN_SMEM;
+}
 
 }  // namespace cheb

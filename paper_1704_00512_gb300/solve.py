@@ -13,7 +13,8 @@ the mu search (Sec. "Fermi Operator Expansion"):
   5. pass 1: the recursion on H~' with the trace functional g_k = <T_k, G>,
      G = (P_out(S^-1/2 P_out(S S^-1/2)))^T, so that Tr(F(mu) S) = sum_k c_k(mu) g_k;
   6. bisection for Tr(F S) = N_e on g (no new products);
-  7. pass 2: the recursion again, accumulating p at mu*;
+  7. pass 2: the recursion again, accumulating p at mu* (and, with n_mu = 4,
+     at three more mu of a 4-point stencil around it);
   8. F = P_out(S^-1/2 P_out(p S^-1/2)) and Tr(F S).
 Host code only sequences calls and moves a few scalars (bounds, degree, mu).
 """
@@ -135,11 +136,13 @@ def postprocess(pb: Problem, A: torch.Tensor, p: torch.Tensor) -> torch.Tensor:
 
 def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FERMI, n_max: int = 16384,
         lanczos_k: int = 40, tol_N: float | None = None, bounds_S=None, n_S=None, bounds_H=None, n_H=None,
-        max_iter: int = 100, timings: dict | None = None) -> dict:
+        max_iter: int = 100, n_mu: int = 1, mu_stencil: float = 0.05, tol_S: float | None = None,
+        timings: dict | None = None) -> dict:
     """Density matrix F with Tr(F S) = N_e (see the module docstring for the steps)."""
     tm = {} if timings is None else timings
     t0 = time.perf_counter()
-    pw = powers(pb, exponents=(-0.5,), tol=tol, bounds_S=bounds_S, n_terms=n_S, precision=L.F64)
+    pw = powers(pb, exponents=(-0.5,), tol=tol if tol_S is None else tol_S, bounds_S=bounds_S, n_terms=n_S,
+                precision=L.F64)
     A = pw["acc"][0]
     Hp = orthogonalise(pb, A)
     if bounds_H is None:
@@ -156,20 +159,30 @@ def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FE
     tm["setup_s"] = time.perf_counter() - t0
     t = torch.zeros(n, dtype=torch.float64, device=pb.device)
     g = torch.zeros(n, dtype=torch.float64, device=pb.device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
     ws = L.expand(pb.planX, Hpt, n, None, [], moments=t, G=G, gmoments=g, precision=pb.precision)
+    ev[1].record()
     if tol_N is None:
         tol_N = 1e-9 * N_e if pb.precision == L.F64 else 1e-6 * N_e
     res = L.mu_search(g, n, e0, e1, kind, kT, N_e, tol_N, max_iter)
     r = L.decode_mu_result(res)
     mu = r["mu"]
-    _, c = L.coeffs([{"kind": kind, "mu": mu, "kT": kT}], e0, e1, 0.0, n, device=pb.device)
-    p = pb.zeros_out()
-    L.expand(pb.planX, Hpt, n, c, [p], precision=pb.precision, ws=ws)
+    # pass 2 accumulates F at mu* and at the three neighbours of the 4-point
+    # stencil mu* + {-1, 1, 2} h, h = mu_stencil * kT (n_mu = 4 simultaneous mu)
+    mus = [mu] + ([mu + d * mu_stencil * kT for d in (-1.0, 1.0, 2.0)] if n_mu == 4 else [])
+    _, c = L.coeffs([{"kind": kind, "mu": m, "kT": kT} for m in mus], e0, e1, 0.0, n, device=pb.device)
+    accs = [pb.zeros_out() for _ in mus]
+    ev[2].record()
+    L.expand(pb.planX, Hpt, n, c, accs, precision=pb.precision, ws=ws)
+    ev[3].record()
+    p = accs[0]
     F = postprocess(pb, A, p)
     trFS = L.trace(pb.P_out.with_vals(F), pb.S)
-    return {"F": F, "p": p, "A": A, "Hp": Hp, "G": G, "mu": mu, "mu_result": r, "moments": t, "gmoments": g,
-            "n_terms": n, "bounds_H": (e0, e1), "bounds_S": pw["bounds"], "n_S": pw["n_terms"],
-            "trace_FS": trFS}
+    tm["events"] = ev
+    return {"F": F, "p": p, "acc_mu": accs, "mus": mus, "A": A, "Hp": Hp, "G": G, "mu": mu, "mu_result": r,
+            "moments": t, "gmoments": g, "n_terms": n, "bounds_H": (e0, e1), "bounds_S": pw["bounds"],
+            "n_S": pw["n_terms"], "trace_FS": trFS}
 
 
 def foe_solve(sysm, r_buf: float, kT: float, N_e: float, tol: float = 1e-10, precision: int = L.F64,

@@ -168,6 +168,12 @@ def _overlap_blocks(xyz, L, I, J, r_cut, exps):
     d = min_image(d, L)
     out = np.zeros((len(I), BS, BS))
     rc2 = r_cut * r_cut
+    if L > 2.0 * r_cut:
+        # every other periodic image is farther than L - L/2 > r_cut
+        r2 = (d * d).sum(axis=1)
+        use = r2 <= rc2
+        out[use] = pref[None] * np.exp(-red[None] * r2[use, None, None])
+        return out
     # Sum over periodic images with distance <= r_cut (only the minimum image
     # unless L < 2 r_cut).
     for nx in (-1, 0, 1):

@@ -50,7 +50,7 @@ def test_invalid_arguments_fail_before_any_cuda_call():
     assert "bad arguments" in lib.cheb_last_error().decode()
     h = ctypes.c_void_p()
     nb = ctypes.c_size_t()
-    assert lib.cheb_plan_create(None, L.F64, ctypes.byref(h), ctypes.byref(nb), None) == L.ERR_INVALID
+    assert lib.cheb_plan_create(None, L.F64, -1, ctypes.byref(h), ctypes.byref(nb), None) == L.ERR_INVALID
     assert lib.cheb_bounds_workspace_size(10, 0, ctypes.byref(nb)) == L.ERR_INVALID
     assert lib.cheb_bounds_workspace_size(10, 40, ctypes.byref(nb)) == L.OK and nb.value > 0
     assert lib.cheb_coeffs_workspace_size(1, 8, ctypes.byref(nb)) == L.ERR_INVALID

@@ -316,3 +316,22 @@ def test_invalid_pattern_and_workspace_errors():
     with pytest.raises(cg.ChebError) as e:
         cg.Plan(cg.Bsr(rp2, ci2), cg.F64)
     assert "symmetric" in str(e.value)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_every_tile_shape_matches(prec):
+    n, nf = 40, 2
+    s, H, P_out, e0, e1, Ht, coeffs, G = _expand_case(150, 5.0, 3.0, 21, n, nf)
+    ex = ref.chebyshev_expand(Ht, P_out, coeffs, G=G)
+    dP = dbsr(P_out.row_ptr, P_out.col_idx)
+    dHt = dbsr(Ht.row_ptr, Ht.col_idx, Ht.vals)
+    tol = 1e-10 if prec == cg.F64 else 1e-5
+    for tile in range(len(cg.tile_shapes(prec))):
+        plan = cg.Plan(dP, prec, tile)
+        acc = [torch.zeros((P_out.nnzb, 4, 4), dtype=torch.float64, device=DEV) for _ in range(nf)]
+        g = torch.zeros(n, dtype=torch.float64, device=DEV)
+        cg.expand(plan, dHt, n, torch.as_tensor(coeffs, device=DEV), acc, G=torch.as_tensor(G.vals, device=DEV),
+                  gmoments=g, precision=prec)
+        for j in range(nf):
+            assert relF(acc[j].cpu().numpy(), ex.acc[j].vals) < tol, (tile, j)
+        assert relF(g.cpu().numpy(), ex.g) < tol
