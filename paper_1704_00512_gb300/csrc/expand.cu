@@ -87,6 +87,34 @@ __device__ __forceinline__ void lds4<double>(double (&x)[4], const double *p) {
     x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
 }
 
+// 16-byte asynchronous global->shared copy (sm_80+ cp.async, L2 only).
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void lds16(T (&h)[16], const T *p);
+template <>
+__device__ __forceinline__ void lds16<float>(float (&h)[16], const float *p) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 v = reinterpret_cast<const float4 *>(p)[i];
+        h[4 * i] = v.x; h[4 * i + 1] = v.y; h[4 * i + 2] = v.z; h[4 * i + 3] = v.w;
+    }
+}
+template <>
+__device__ __forceinline__ void lds16<double>(double (&h)[16], const double *p) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const double2 v = reinterpret_cast<const double2 *>(p)[i];
+        h[2 * i] = v.x; h[2 * i + 1] = v.y;
+    }
+}
+
 __device__ __forceinline__ int rank_of(const uint2 *bits, int K) {
     const uint2 w = bits[K >> 5];
     const unsigned bit = 1u << (K & 31);
@@ -223,6 +251,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
     int32_t *ulist = reinterpret_cast<int32_t *>(smem + lay.off_ulist);
     int16_t *pos = reinterpret_cast<int16_t *>(smem + lay.off_pos);
     int2 *wlist = reinterpret_cast<int2 *>(smem + lay.off_wl);
+    int *bslot = reinterpret_cast<int *>(smem + lay.off_bslot);
+    T *hbuf = reinterpret_cast<T *>(smem + lay.off_hbuf);
     T *X = reinterpret_cast<T *>(smem + lay.off_x);
     double *red = reinterpret_cast<double *>(smem + lay.off_red);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -284,28 +314,39 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
 
     // 3. union rows: masked block products M~_I. X for the panel's columns.
     // The row's blocks are ranked 32 at a time (one block per lane); those
-    // whose column K is in the union are appended to the warp's staging ring.
-    // Whenever 32 entries are staged, each K-group takes NU of them, issues
-    // their loads back to back and then does the FMAs, so every batch but the
-    // row's last is full and the loads of a batch are in flight together.
+    // whose column K is in the union go to the warp's staging ring.  Every 32
+    // staged entries form a batch whose operator blocks are copied to shared
+    // memory with asynchronous copies (cp.async); the batch before it is
+    // multiplied while they are in flight.  In a batch each K-group takes NU
+    // entries; a lane multiplies the 4x4 operator block by the panel block of
+    // its column q.
     {
         const int q = lane % P, kg = lane / P;
         const unsigned lt = (1u << lane) - 1u;
         int2 *wl = wlist + warp * 64;
-        auto batch = [&](T(&acc)[16], int navail) {
-            int2 en[NU];
-            T h[NU][16];
+        T *hb = hbuf + (size_t)warp * 2 * 32 * BB;  // two batches of 32 staged blocks
+        int *bs = bslot + warp * 64;                 // union slots of the staged blocks
+        auto issue = [&](int buf, int n) {
+            if (lane < n) {
+                const int2 e = wl[lane];
+                bs[buf * 32 + lane] = e.y;
+                const T *src = a.Lv + (int64_t)e.x * BB;
+                T *dst = hb + ((size_t)buf * 32 + lane) * BB;
+#pragma unroll
+                for (int c = 0; c < (int)(BB * sizeof(T) / 16); ++c) cp_async16(dst + c * (16 / sizeof(T)), src + c * (16 / sizeof(T)));
+            }
+            cp_async_commit();
+        };
+        auto compute = [&](T(&acc)[16], int buf, int n) {
 #pragma unroll
             for (int u = 0; u < NU; ++u) {
                 const int e = u * KG + kg;
-                en[u] = e < navail ? wl[e] : make_int2(-1, 0);
-                if (en[u].x >= 0) load16<T>(h[u], a.Lv + (int64_t)en[u].x * BB);
-            }
-#pragma unroll
-            for (int u = 0; u < NU; ++u) {
-                if (en[u].x < 0) continue;
-                const T *xs = X + en[u].y * (BB * P) + 4 * q;
-                const int sw = en[u].y & 1;
+                if (e >= n) continue;
+                T h[16];
+                lds16<T>(h, hb + ((size_t)buf * 32 + e) * BB);
+                const int s2 = bs[buf * 32 + e];
+                const T *xs = X + s2 * (BB * P) + 4 * q;
+                const int sw = s2 & 1;
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     T x[4];
@@ -313,7 +354,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) acc[4 * r + c] = fma(h[u][4 * r + m], x[c], acc[4 * r + c]);
+                        for (int c = 0; c < 4; ++c) acc[4 * r + c] = fma(h[4 * r + m], x[c], acc[4 * r + c]);
                 }
             }
         };
@@ -323,7 +364,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
             T acc[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) acc[i] = T(0);
-            int pending = 0;
+            int pending = 0, inflight = -1, n_inflight = 0, nb = 0;
             int64_t base = a0;
             int Knext = (a0 + lane < a1) ? a.Lci[a0 + lane] : -1;
             while (true) {
@@ -340,17 +381,31 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
                 const bool raw_done = base >= a1;
                 if (pending >= 32 || (raw_done && pending > 0)) {
                     const int n = pending < 32 ? pending : 32;
-                    batch(acc, n);
+                    issue(nb, n);
                     __syncwarp();
                     const int rest = pending - n;
                     const int2 keep = lane < rest ? wl[n + lane] : make_int2(0, 0);
                     __syncwarp();
                     if (lane < rest) wl[lane] = keep;
                     pending = rest;
+                    if (inflight >= 0) {
+                        cp_async_wait<1>();
+                        __syncwarp();
+                        compute(acc, inflight, n_inflight);
+                    }
+                    inflight = nb;
+                    n_inflight = n;
+                    nb ^= 1;
                     __syncwarp();
                 }
                 if (raw_done && pending == 0) break;
             }
+            if (inflight >= 0) {
+                cp_async_wait<0>();
+                __syncwarp();
+                compute(acc, inflight, n_inflight);
+            }
+            __syncwarp();
 #pragma unroll
             for (int o = P; o < 32; o <<= 1)
 #pragma unroll

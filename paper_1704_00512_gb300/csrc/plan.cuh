@@ -36,7 +36,7 @@ namespace cheb {
 // Shared-memory layout of the step kernel for a panel of width P over a union of
 // ucap rows, element size esz, nw bitmap words, nwarps warps.
 struct StepLayout {
-    size_t off_bits, off_ulist, off_pos, off_wl, off_x, off_red, total;
+    size_t off_bits, off_ulist, off_pos, off_wl, off_bslot, off_hbuf, off_x, off_red, total;
 };
 
 __host__ __device__ inline StepLayout step_layout(int64_t nw, int64_t ucap, int P, int esz, int nwarps) {
@@ -53,6 +53,11 @@ __host__ __device__ inline StepLayout step_layout(int64_t nw, int64_t ucap, int 
     o = (o + 15) / 16 * 16;
     L.off_wl = o;
     o += (size_t)nwarps * 64 * 8;  // per-warp ring of staged (block index, union slot) pairs
+    L.off_bslot = o;
+    o += (size_t)nwarps * 64 * 4;  // union slots of the two staged batches
+    o = (o + 127) / 128 * 128;
+    L.off_hbuf = o;
+    o += (size_t)nwarps * 2 * 32 * BB * esz;  // two batches of 32 operator blocks per warp
     o = (o + 15) / 16 * 16;
     L.off_x = o;
     o += (size_t)ucap * BB * P * esz;  // the gathered panel of T_k
@@ -68,8 +73,8 @@ __host__ __device__ inline StepLayout step_layout(int64_t nw, int64_t ucap, int 
 struct TileCfg {
     int P, NW, MINB;
 };
-constexpr TileCfg TILES_F32[] = {{4, 16, 1}, {4, 8, 1}, {2, 8, 2}, {2, 8, 3}, {2, 16, 1}, {1, 8, 3}};
-constexpr TileCfg TILES_F64[] = {{2, 8, 1}, {1, 8, 2}, {2, 4, 2}, {1, 4, 3}, {2, 16, 1}};
+constexpr TileCfg TILES_F32[] = {{4, 8, 1}, {4, 16, 1}, {4, 12, 1}, {2, 8, 2}, {2, 4, 3}, {1, 8, 3}};
+constexpr TileCfg TILES_F64[] = {{2, 8, 1}, {2, 4, 2}, {1, 8, 2}, {1, 4, 3}, {2, 16, 1}};
 constexpr int N_TILES_F32 = sizeof(TILES_F32) / sizeof(TileCfg);
 constexpr int N_TILES_F64 = sizeof(TILES_F64) / sizeof(TileCfg);
 inline int n_tiles(int precision) { return precision == CHEB_F64 ? N_TILES_F64 : N_TILES_F32; }
