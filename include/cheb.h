@@ -127,7 +127,9 @@ int cheb_pattern_build(const double *xyz, int64_t n_atoms, double box_L, double 
  * (>= plan_ws_bytes, 256-byte aligned); the plan then refers to that memory,
  * which must stay valid until cheb_plan_destroy.  P_out's row_ptr/col_idx
  * pointers are remembered by the plan and must stay valid too.
- * cheb_plan_info reports (n_panels, panel width, max panel union rows).
+ * cheb_plan_info reports (n_panels, panel width, max panel union rows) of the
+ * per-step kernel; cheb_plan_resident_info (n_panels, max union rows, max
+ * blocks per panel) of the resident expansion kernel.
  */
 typedef struct cheb_plan cheb_plan;
 
@@ -195,16 +197,58 @@ int cheb_coeffs(const cheb_func *funcs, int32_t n_f, double emin, double emax, d
  *   moments, gmoments: device double[n_terms] or NULL; G: device double on
  *   P_out or NULL.  precision: CHEB_F64 (T_k and products in FP64) or CHEB_F32
  *   (Mt rounded to FP32, T_k stored and multiplied in FP32, accumulators and
- *   moments in FP64).  Asynchronous.  Workspace: cheb_expand_workspace_size.
+ *   moments in FP64).  Results are bitwise reproducible run to run.
+ *
+ * cheb_expand runs the whole expansion in one kernel launch: every thread
+ * block owns a panel of block columns (columns are independent under Eq. 3)
+ * and keeps its T_k, T_{k-1} in shared memory for all steps; there is no
+ * inter-block synchronisation.  Asynchronous, graph-capturable (no host
+ * copies).  Workspace: cheb_expand_workspace_size with max_terms >= n_terms.
  * Errors: CHEB_ERR_INVALID (n_terms < 2, n_f < 0 or > 8, plan precision !=
- * precision), CHEB_ERR_NOSPACE (workspace too small).
+ * precision, batched plan), CHEB_ERR_NOSPACE (workspace too small).
  */
 int cheb_expand_workspace_size(const cheb_plan *plan, const cheb_bsr *Mt, int32_t precision,
-                               size_t *bytes);
+                               int32_t max_terms, size_t *bytes);
 int cheb_expand(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_terms,
                 const double *coeffs, int32_t coeff_stride, int32_t n_f, double *const *acc,
                 double *moments, const double *G, double *gmoments, int32_t precision,
                 void *ws, size_t ws_bytes, void *stream);
+
+/* The same expansion as one kernel launch per step (T_k in HBM, three
+ * P_out-sized buffers in the workspace).  Same arguments and results up to
+ * rounding order; kept as an independent second implementation and for
+ * plans whose panels do not fit the resident kernel. */
+int cheb_expand_stepwise_workspace_size(const cheb_plan *plan, const cheb_bsr *Mt,
+                                        int32_t precision, size_t *bytes);
+int cheb_expand_stepwise(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_terms,
+                         const double *coeffs, int32_t coeff_stride, int32_t n_f,
+                         double *const *acc, double *moments, const double *G, double *gmoments,
+                         int32_t precision, void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched expansion: many independent systems of uneven size in one launch.
+ * The caller concatenates the systems block-diagonally (block rows of system
+ * i are sys_row_start[i] .. sys_row_start[i+1]-1, each system's operator
+ * already scaled with its own bounds) and creates the plan with
+ * cheb_plan_create_batched so that no panel straddles two systems.  System i
+ * runs n_terms[i] terms (device int32[nsys], max_terms >= all of them) with
+ * coefficients coeffs + coeff_offset[i] (device int64[nsys]; layout
+ * [n_f][coeff_stride] per system); moments of system i go to
+ * moments/gmoments + i*moment_stride.  acc / G are on the concatenated P_out.
+ * One kernel launch for all systems and all steps (plus one moment reduction);
+ * asynchronous and graph-capturable.
+ */
+int cheb_plan_create_batched(const cheb_bsr *P_out, int32_t precision, int32_t tile,
+                             int32_t nsys, const int64_t *sys_row_start, cheb_plan **plan,
+                             size_t *plan_ws_bytes, void *stream);
+int cheb_plan_resident_info(const cheb_plan *plan, int64_t *n_panels, int32_t *max_union,
+                            int32_t *max_blocks);
+int cheb_expand_batched(const cheb_plan *plan, const cheb_bsr *Mt, int32_t max_terms,
+                        const int32_t *n_terms, const double *coeffs,
+                        const int64_t *coeff_offset, int32_t coeff_stride, int32_t n_f,
+                        double *const *acc, double *moments, const double *G, double *gmoments,
+                        int32_t moment_stride, int32_t precision, void *ws, size_t ws_bytes,
+                        void *stream);
 
 /* ---------------------------------------------------------------------------
  * One masked product (the building block of Eq. 3 outside the recursion):
@@ -220,14 +264,15 @@ int cheb_masked_product(const cheb_plan *plan, const cheb_bsr *L, const double *
  * not alias A.  Asynchronous. */
 int cheb_transpose(const cheb_plan *plan, const double *A, double *out, void *stream);
 
-/* Keep the blocks of A (FP64 on pattern PA) that lie in pattern P (contained
- * in PA): out = device double[P->nnzb*16].  Asynchronous. */
+/* Keep the blocks of A (FP64 on pattern PA) that lie in pattern P: out = device
+ * double[P->nnzb*16]; blocks of P outside PA are written as zero.
+ * Asynchronous. */
 int cheb_restrict(const cheb_bsr *A, const cheb_bsr *P, double *out, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Trace (Sec. "Fermi Operator Expansion": Tr(KS) = N).  out (device double[1])
  * = sum over the blocks (i,j) of B's pattern of A_ij * B_ij, which is Tr(A B)
- * for symmetric B.  B's pattern must be contained in A's.  FP64.
+ * for symmetric B; blocks of B outside A's pattern count as zero.  FP64.
  * Asynchronous.  Workspace: cheb_trace_workspace_size.
  */
 int cheb_trace_workspace_size(const cheb_bsr *B, size_t *bytes);

@@ -28,6 +28,8 @@ EXPORTS = [
     "cheb_last_error", "cheb_launch_count", "cheb_pattern_build", "cheb_tile_count", "cheb_tile_info", "cheb_plan_create", "cheb_plan_bind", "cheb_plan_info",
     "cheb_plan_destroy", "cheb_scale", "cheb_bounds_workspace_size", "cheb_bounds",
     "cheb_coeffs_workspace_size", "cheb_coeffs", "cheb_expand_workspace_size", "cheb_expand",
+    "cheb_expand_stepwise_workspace_size", "cheb_expand_stepwise", "cheb_plan_create_batched",
+    "cheb_plan_resident_info", "cheb_expand_batched",
     "cheb_masked_product", "cheb_transpose", "cheb_restrict", "cheb_trace_workspace_size", "cheb_trace",
     "cheb_penalty_trace", "cheb_mu_search", "cheb_newton_schulz",
 ]
@@ -79,8 +81,13 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
         "cheb_bounds": ([P(CBsr), i32, p, dbl, P(dbl), P(dbl), P(dbl), p, sz, p], i32),
         "cheb_coeffs_workspace_size": ([i32, i32, P(sz)], i32),
         "cheb_coeffs": ([P(CFunc), i32, dbl, dbl, dbl, i32, i32, P(i32), p, p, sz, p], i32),
-        "cheb_expand_workspace_size": ([p, P(CBsr), i32, P(sz)], i32),
+        "cheb_expand_workspace_size": ([p, P(CBsr), i32, i32, P(sz)], i32),
         "cheb_expand": ([p, P(CBsr), i32, p, i32, i32, P(p), p, p, p, i32, p, sz, p], i32),
+        "cheb_expand_stepwise_workspace_size": ([p, P(CBsr), i32, P(sz)], i32),
+        "cheb_expand_stepwise": ([p, P(CBsr), i32, p, i32, i32, P(p), p, p, p, i32, p, sz, p], i32),
+        "cheb_plan_create_batched": ([P(CBsr), i32, i32, i32, P(i64), P(p), P(sz), p], i32),
+        "cheb_plan_resident_info": ([p, P(i64), P(i32), P(i32)], i32),
+        "cheb_expand_batched": ([p, P(CBsr), i32, p, p, p, i32, i32, P(p), p, p, p, i32, i32, p, sz, p], i32),
         "cheb_masked_product": ([p, P(CBsr), p, dbl, p, dbl, p, p], i32),
         "cheb_transpose": ([p, p, p, p], i32),
         "cheb_restrict": ([P(CBsr), P(CBsr), p, p], i32),
@@ -258,28 +265,82 @@ def coeffs(funcs, emin: float, emax: float, tol: float, n_max: int, rel: bool = 
     return n.value, out
 
 
-def expand_workspace_size(plan: Plan, Mt: Bsr, precision: int) -> int:
+def expand_workspace_size(plan: Plan, Mt: Bsr, precision: int, max_terms: int) -> int:
     nb = ctypes.c_size_t(0)
     cb = Mt.c()
-    _check(load().cheb_expand_workspace_size(plan.handle, ctypes.byref(cb), precision, ctypes.byref(nb)))
+    _check(load().cheb_expand_workspace_size(plan.handle, ctypes.byref(cb), precision, max_terms, ctypes.byref(nb)))
     return nb.value
 
 
 def expand(plan: Plan, Mt: Bsr, n_terms: int, coeffs: torch.Tensor | None, acc: list[torch.Tensor],
            moments: torch.Tensor | None = None, G: torch.Tensor | None = None, gmoments: torch.Tensor | None = None,
-           precision: int = F64, ws: torch.Tensor | None = None, stream=None):
-    """cheb_expand.  acc: list of FP64 tensors on P_out (overwritten)."""
+           precision: int = F64, ws: torch.Tensor | None = None, stream=None, stepwise: bool = False):
+    """cheb_expand (one launch, resident panels) or cheb_expand_stepwise.  acc: FP64 tensors on P_out."""
     lib = load()
-    need = expand_workspace_size(plan, Mt, precision)
+    cb = Mt.c()
+    nb = ctypes.c_size_t(0)
+    if stepwise:
+        _check(lib.cheb_expand_stepwise_workspace_size(plan.handle, ctypes.byref(cb), precision, ctypes.byref(nb)))
+    else:
+        _check(lib.cheb_expand_workspace_size(plan.handle, ctypes.byref(cb), precision, n_terms, ctypes.byref(nb)))
+    need = nb.value
     if ws is None or ws.numel() < need + 256:
         ws = _ws(need, Mt.vals.device)
     nf = len(acc)
     arr = (ctypes.c_void_p * max(nf, 1))(*[t.data_ptr() for t in acc])
     stride = coeffs.shape[1] if coeffs is not None else n_terms
+    fn = lib.cheb_expand_stepwise if stepwise else lib.cheb_expand
+    _check(fn(plan.handle, ctypes.byref(cb), n_terms, _ptr(coeffs), stride, nf, arr, _ptr(moments), _ptr(G),
+              _ptr(gmoments), precision, ctypes.c_void_p(_aligned(ws)), need, _stream(stream)))
+    return ws
+
+
+class BatchedPlan(Plan):
+    """cheb_plan_create_batched: block-diagonal systems, panels never straddle two systems."""
+
+    def __init__(self, P_out: Bsr, sys_row_start, precision: int = F32, tile: int = -1, stream=None):
+        lib = load()
+        self.P_out = P_out
+        self.precision = precision
+        self.tile = tile
+        starts = (ctypes.c_int64 * len(sys_row_start))(*[int(x) for x in sys_row_start])
+        self.nsys = len(sys_row_start) - 1
+        h = ctypes.c_void_p()
+        nbytes = ctypes.c_size_t(0)
+        s = _stream(stream)
+        cb = P_out.c()
+        _check(lib.cheb_plan_create_batched(ctypes.byref(cb), precision, tile, self.nsys, starts, ctypes.byref(h),
+                                            ctypes.byref(nbytes), s))
+        self.handle = h
+        self._ws = _ws(nbytes.value, P_out.row_ptr.device)
+        _check(lib.cheb_plan_bind(h, ctypes.c_void_p(_aligned(self._ws)), nbytes.value, s))
+
+
+def plan_resident_info(plan: Plan) -> tuple[int, int, int]:
+    a, b, c = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().cheb_plan_resident_info(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def expand_batched(plan: BatchedPlan, Mt: Bsr, max_terms: int, n_terms: torch.Tensor, coeffs: torch.Tensor | None,
+                   coeff_offset: torch.Tensor | None, coeff_stride: int, acc: list[torch.Tensor],
+                   moments: torch.Tensor | None = None, G: torch.Tensor | None = None,
+                   gmoments: torch.Tensor | None = None, moment_stride: int = 0, precision: int = F32,
+                   ws: torch.Tensor | None = None, stream=None):
+    """cheb_expand_batched: every system of the block-diagonal batch in one launch."""
+    lib = load()
     cb = Mt.c()
-    _check(lib.cheb_expand(plan.handle, ctypes.byref(cb), n_terms, _ptr(coeffs), stride, nf, arr, _ptr(moments),
-                           _ptr(G), _ptr(gmoments), precision, ctypes.c_void_p(_aligned(ws)), need,
-                           _stream(stream)))
+    nb = ctypes.c_size_t(0)
+    _check(lib.cheb_expand_workspace_size(plan.handle, ctypes.byref(cb), precision, max_terms, ctypes.byref(nb)))
+    need = nb.value
+    if ws is None or ws.numel() < need + 256:
+        ws = _ws(need, Mt.vals.device)
+    nf = len(acc)
+    arr = (ctypes.c_void_p * max(nf, 1))(*[t.data_ptr() for t in acc])
+    _check(lib.cheb_expand_batched(plan.handle, ctypes.byref(cb), max_terms, _ptr(n_terms), _ptr(coeffs),
+                                   _ptr(coeff_offset), coeff_stride, nf, arr, _ptr(moments), _ptr(G), _ptr(gmoments),
+                                   moment_stride or max_terms, precision, ctypes.c_void_p(_aligned(ws)), need,
+                                   _stream(stream)))
     return ws
 
 

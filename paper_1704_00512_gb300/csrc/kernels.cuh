@@ -1,0 +1,197 @@
+// Device helpers shared by the recursion kernels (expand.cu, resident.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace cheb {
+
+constexpr int MAX_F = 8;  // accumulators (functions / mu values) per expansion
+
+template <typename T>
+__device__ __forceinline__ void load16(T (&h)[16], const T *p);
+template <>
+__device__ __forceinline__ void load16<float>(float (&h)[16], const float *p) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float4 v = __ldg(q + i);
+        h[4 * i] = v.x; h[4 * i + 1] = v.y; h[4 * i + 2] = v.z; h[4 * i + 3] = v.w;
+    }
+}
+template <>
+__device__ __forceinline__ void load16<double>(double (&h)[16], const double *p) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        double2 v = __ldg(q + i);
+        h[2 * i] = v.x; h[2 * i + 1] = v.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void lds4(T (&x)[4], const T *p);
+template <>
+__device__ __forceinline__ void lds4<float>(float (&x)[4], const float *p) {
+    float4 v = *reinterpret_cast<const float4 *>(p);
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void lds4<double>(double (&x)[4], const double *p) {
+    double2 a = *reinterpret_cast<const double2 *>(p);
+    double2 b = *reinterpret_cast<const double2 *>(p + 2);
+    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+}
+
+// 16-byte asynchronous global->shared copy (sm_80+ cp.async, L2 only).
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename T>
+__device__ __forceinline__ void lds16(T (&h)[16], const T *p);
+template <>
+__device__ __forceinline__ void lds16<float>(float (&h)[16], const float *p) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 v = reinterpret_cast<const float4 *>(p)[i];
+        h[4 * i] = v.x; h[4 * i + 1] = v.y; h[4 * i + 2] = v.z; h[4 * i + 3] = v.w;
+    }
+}
+template <>
+__device__ __forceinline__ void lds16<double>(double (&h)[16], const double *p) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const double2 v = reinterpret_cast<const double2 *>(p)[i];
+        h[2 * i] = v.x; h[2 * i + 1] = v.y;
+    }
+}
+
+__device__ __forceinline__ int rank_of(const uint2 *bits, int K) {
+    const uint2 w = bits[K >> 5];
+    const unsigned bit = 1u << (K & 31);
+    if (!(w.x & bit)) return -1;
+    return (int)w.y + __popc(w.x & (bit - 1u));
+}
+
+// Exclusive block scan of one int per thread; returns the prefix, *total = sum.
+template <int NW>
+__device__ __forceinline__ int block_excl_scan(int v, int *wsum, int *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int n = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int x = lane < NW ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int n = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += n;
+        }
+        if (lane < NW) wsum[lane] = x;
+    }
+    __syncthreads();
+    const int excl = incl - v + (warp > 0 ? wsum[warp - 1] : 0);
+    *total = wsum[NW - 1];
+    __syncthreads();
+    return excl;
+}
+
+template <int NV>
+struct Moments {
+    double v[NV];    // this thread's partial sums
+    double *dst[NV];  // device scalars receiving the totals (NULL = not wanted)
+};
+
+// Deterministic sum of the per-block partials by the last block to finish.
+template <int NT, int NV>
+__device__ __forceinline__ void finish_moments(double *part, int32_t *counter, const Moments<NV> m, double *red) {
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double w = warp_sum(m.v[i]);
+        if (lane == 0) red[warp * NV + i] = w;
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < NT / 32; ++w) s += red[w * NV + i];
+            part[(int64_t)blockIdx.x * NV + i] = s;
+        }
+        __threadfence();
+        const int prev = atomicAdd(counter, 1);
+        s_last = prev == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (int b = tid; b < (int)gridDim.x; b += NT) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] += __ldcg(part + (int64_t)b * NV + i);
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double w = warp_sum(acc[i]);
+        if (lane == 0) red[warp * NV + i] = w;
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < NT / 32; ++w) s += red[w * NV + i];
+            if (m.dst[i]) *m.dst[i] = s;
+        }
+        *counter = 0;
+        __threadfence();
+    }
+}
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    static __device__ __forceinline__ void ld(float (&v)[4], const float *p) {
+        float4 a = *reinterpret_cast<const float4 *>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    static __device__ __forceinline__ void ldg(float (&v)[4], const float *p) {
+        float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float (&v)[4]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <>
+struct Vec4<double> {
+    static __device__ __forceinline__ void ld(double (&v)[4], const double *p) {
+        double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void ldg(double (&v)[4], const double *p) {
+        double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p + 2));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void st(double *p, const double (&v)[4]) {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
+    }
+};
+
+
+}  // namespace cheb

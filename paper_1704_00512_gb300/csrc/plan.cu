@@ -42,8 +42,8 @@ extern "C" int cheb_tile_info(int32_t precision, int32_t tile, int32_t *panel_wi
     return CHEB_OK;
 }
 
-extern "C" int cheb_plan_create(const cheb_bsr *P_out, int32_t precision, int32_t tile, cheb_plan **out,
-                                size_t *plan_ws_bytes, void *stream) {
+static int plan_create_impl(const cheb_bsr *P_out, int32_t precision, int32_t tile, int32_t nsys,
+                            const int64_t *sys_row_start, cheb_plan **out, size_t *plan_ws_bytes, void *stream) {
     if (!out || !plan_ws_bytes) return fail(CHEB_ERR_INVALID, "cheb_plan_create: NULL output");
     *out = nullptr;
     if (!P_out || P_out->nbr < 1 || P_out->nnzb < P_out->nbr || !P_out->row_ptr || !P_out->col_idx)
@@ -53,7 +53,20 @@ extern "C" int cheb_plan_create(const cheb_bsr *P_out, int32_t precision, int32_
     if (P_out->nnzb >= (int64_t)INT32_MAX) return fail(CHEB_ERR_INVALID, "cheb_plan_create: too many blocks");
     if (tile < 0) tile = 0;
     if (tile >= n_tiles(precision)) return fail(CHEB_ERR_INVALID, "cheb_plan_create: no tile %d", tile);
+    if (nsys < 1) return fail(CHEB_ERR_INVALID, "cheb_plan_create: nsys < 1");
     const int64_t nbr = P_out->nbr, nnzb = P_out->nnzb;
+    std::vector<int64_t> sys_col(nsys + 1);
+    if (sys_row_start) {
+        for (int i = 0; i <= nsys; ++i) sys_col[i] = sys_row_start[i];
+        if (sys_col[0] != 0 || sys_col[nsys] != nbr)
+            return fail(CHEB_ERR_INVALID, "cheb_plan_create: system row starts must span 0..nbr");
+        for (int i = 0; i < nsys; ++i)
+            if (sys_col[i + 1] <= sys_col[i]) return fail(CHEB_ERR_INVALID, "cheb_plan_create: empty system %d", i);
+    } else {
+        if (nsys != 1) return fail(CHEB_ERR_INVALID, "cheb_plan_create: system row starts missing");
+        sys_col[0] = 0;
+        sys_col[1] = nbr;
+    }
     std::vector<int64_t> rp(nbr + 1);
     std::vector<int32_t> ci(nnzb);
     cudaStream_t s = as_stream(stream);
@@ -77,6 +90,8 @@ extern "C" int cheb_plan_create(const cheb_bsr *P_out, int32_t precision, int32_
     plan->rp = P_out->row_ptr;
     plan->ci = P_out->col_idx;
     plan->precision = precision;
+    plan->nsys = nsys;
+    plan->h_sys_col = sys_col;
     plan->h_tperm.resize(nnzb);
     for (int64_t I = 0; I < nbr; ++I) {
         for (int64_t p = rp[I]; p < rp[I + 1]; ++p) {
@@ -98,40 +113,114 @@ extern "C" int cheb_plan_create(const cheb_bsr *P_out, int32_t precision, int32_
     plan->P = P;
     plan->NW = cfg.NW;
     plan->minb = cfg.MINB;
-    plan->ucap = union_capacity(nbr, P, esz, cfg.NW, smem_budget(cfg.MINB));
-    // greedy panels; stamp[K] = last panel that counted row K
+    const size_t budget = smem_budget(cfg.MINB);
+    plan->ucap = union_capacity(nbr, P, esz, cfg.NW, budget);
+    const int64_t nw = (nbr + 31) / 32;
     std::vector<int32_t> stamp(nbr, -1);
-    int64_t j = 0, panel = 0;
-    int32_t max_union = 0;
-    while (j < nbr) {
-        int32_t cnt = 0, ncols = 0;
-        const int64_t j0 = j;
-        while (j < nbr && ncols < P) {
-            // rows of column j (= columns of row j, the pattern being symmetric)
-            int32_t add = 0;
-            for (int64_t p = rp[j]; p < rp[j + 1]; ++p) add += stamp[ci[p]] != (int32_t)panel;
-            if (ncols > 0 && cnt + add > plan->ucap) break;
-            if (cnt + add > plan->ucap) {
-                delete plan;
-                return fail(CHEB_ERR_NOSPACE, "column %lld has %d rows, shared-memory panel holds %d",
-                            (long long)j, add, plan->ucap);
+    // step-kernel panels: greedy along the columns while the union fits
+    {
+        int64_t j = 0, panel = 0;
+        int32_t max_union = 0;
+        while (j < nbr) {
+            int32_t cnt = 0, ncols = 0;
+            const int64_t j0 = j;
+            while (j < nbr && ncols < P) {
+                int32_t add = 0;
+                for (int64_t p = rp[j]; p < rp[j + 1]; ++p) add += stamp[ci[p]] != (int32_t)panel;
+                if (ncols > 0 && cnt + add > plan->ucap) break;
+                if (cnt + add > plan->ucap) {
+                    delete plan;
+                    return fail(CHEB_ERR_NOSPACE, "column %lld has %d rows, shared-memory panel holds %d",
+                                (long long)j, add, plan->ucap);
+                }
+                for (int64_t p = rp[j]; p < rp[j + 1]; ++p) stamp[ci[p]] = (int32_t)panel;
+                cnt += add;
+                ++ncols;
+                ++j;
             }
-            for (int64_t p = rp[j]; p < rp[j + 1]; ++p) stamp[ci[p]] = (int32_t)panel;
-            cnt += add;
-            ++ncols;
-            ++j;
+            plan->h_panels.push_back((int32_t)j0);
+            plan->h_panels.push_back(ncols);
+            max_union = std::max(max_union, cnt);
+            ++panel;
         }
-        plan->h_panels.push_back((int32_t)j0);
-        plan->h_panels.push_back(ncols);
-        max_union = std::max(max_union, cnt);
-        ++panel;
+        plan->n_panels = panel;
+        plan->max_union = max_union;
     }
-    plan->n_panels = panel;
-    plan->max_union = max_union;
-    plan->ws_bytes = align_up(nnzb * 4) + align_up(plan->h_panels.size() * 4) + align_up(64);
+    // resident panels: greedy within each system while the panel's union and
+    // block count stay under caps (Ucap, Bcap) whose layout fits the budget,
+    // so that the launch (sized by the maxima over panels) fits as well
+    {
+        int32_t maxlen = 1;
+        for (int64_t j = 0; j < nbr; ++j) maxlen = std::max(maxlen, (int32_t)(rp[j + 1] - rp[j]));
+        auto bcap_for = [&](int64_t ucap) {
+            int64_t lo = 0, hi = (int64_t)P * maxlen;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) / 2;
+                if (res_layout(nw, ucap, mid, P, esz, cfg.NW).total <= budget) lo = mid; else hi = mid - 1;
+            }
+            return lo;
+        };
+        int64_t Ucap = std::min<int64_t>(2 * (int64_t)maxlen, 32767);
+        int64_t Bcap = bcap_for(Ucap);
+        while (Bcap < maxlen && Ucap > maxlen) {
+            Ucap = std::max<int64_t>(maxlen, Ucap * 3 / 4);
+            Bcap = bcap_for(Ucap);
+        }
+        if (Bcap < maxlen) {
+            delete plan;
+            return fail(CHEB_ERR_NOSPACE, "a column of %d blocks does not fit a resident panel", maxlen);
+        }
+        std::fill(stamp.begin(), stamp.end(), -1);
+        int64_t panel = 0;
+        int32_t max_union = 0, max_nblk = 0;
+        for (int sy = 0; sy < nsys; ++sy) {
+            plan->h_sys_rpanel.push_back((int32_t)panel);
+            int64_t j = sys_col[sy];
+            while (j < sys_col[sy + 1]) {
+                int32_t cnt = 0, ncols = 0, nblk = 0;
+                const int64_t j0 = j;
+                while (j < sys_col[sy + 1] && ncols < P) {
+                    int32_t add = 0;
+                    const int32_t len = (int32_t)(rp[j + 1] - rp[j]);
+                    for (int64_t p = rp[j]; p < rp[j + 1]; ++p) add += stamp[ci[p]] != (int32_t)panel;
+                    if (ncols > 0 && (cnt + add > Ucap || nblk + len > Bcap)) break;
+                    for (int64_t p = rp[j]; p < rp[j + 1]; ++p) stamp[ci[p]] = (int32_t)panel;
+                    cnt += add;
+                    nblk += len;
+                    ++ncols;
+                    ++j;
+                }
+                plan->h_rpanels.push_back((int32_t)j0);
+                plan->h_rpanels.push_back(ncols);
+                plan->h_rpanel_sys.push_back(sy);
+                max_union = std::max(max_union, cnt);
+                max_nblk = std::max(max_nblk, nblk);
+                ++panel;
+            }
+        }
+        plan->h_sys_rpanel.push_back((int32_t)panel);
+        plan->n_rpanels = panel;
+        plan->max_union_res = max_union;
+        plan->max_nblk_res = max_nblk;
+    }
+    plan->ws_bytes = align_up(nnzb * 4) + align_up(plan->h_panels.size() * 4) + align_up(64) +
+                     align_up(plan->h_rpanels.size() * 4) + align_up(plan->h_rpanel_sys.size() * 4) +
+                     align_up(plan->h_sys_rpanel.size() * 4);
     *plan_ws_bytes = plan->ws_bytes;
     *out = plan;
     return CHEB_OK;
+}
+
+extern "C" int cheb_plan_create(const cheb_bsr *P_out, int32_t precision, int32_t tile, cheb_plan **out,
+                                size_t *plan_ws_bytes, void *stream) {
+    return plan_create_impl(P_out, precision, tile, 1, nullptr, out, plan_ws_bytes, stream);
+}
+
+extern "C" int cheb_plan_create_batched(const cheb_bsr *P_out, int32_t precision, int32_t tile, int32_t nsys,
+                                        const int64_t *sys_row_start, cheb_plan **out, size_t *plan_ws_bytes,
+                                        void *stream) {
+    if (!sys_row_start) return fail(CHEB_ERR_INVALID, "cheb_plan_create_batched: sys_row_start is NULL");
+    return plan_create_impl(P_out, precision, tile, nsys, sys_row_start, out, plan_ws_bytes, stream);
 }
 
 extern "C" int cheb_plan_bind(cheb_plan *plan, void *ws, size_t ws_bytes, void *stream) {
@@ -143,11 +232,20 @@ extern "C" int cheb_plan_bind(cheb_plan *plan, void *ws, size_t ws_bytes, void *
     plan->d_tperm = cv.take<int32_t>(plan->nnzb);
     plan->d_panels = cv.take<int32_t>(plan->h_panels.size());
     plan->d_counter = cv.take<int32_t>(16);
+    plan->d_rpanels = cv.take<int32_t>(plan->h_rpanels.size());
+    plan->d_rpanel_sys = cv.take<int32_t>(plan->h_rpanel_sys.size());
+    plan->d_sys_rpanel = cv.take<int32_t>(plan->h_sys_rpanel.size());
     cudaStream_t s = as_stream(stream);
     CHEB_CUDA(cudaMemcpyAsync(plan->d_tperm, plan->h_tperm.data(), plan->nnzb * 4, cudaMemcpyHostToDevice, s));
     CHEB_CUDA(cudaMemcpyAsync(plan->d_panels, plan->h_panels.data(), plan->h_panels.size() * 4,
                               cudaMemcpyHostToDevice, s));
     CHEB_CUDA(cudaMemsetAsync(plan->d_counter, 0, 64, s));
+    CHEB_CUDA(cudaMemcpyAsync(plan->d_rpanels, plan->h_rpanels.data(), plan->h_rpanels.size() * 4,
+                              cudaMemcpyHostToDevice, s));
+    CHEB_CUDA(cudaMemcpyAsync(plan->d_rpanel_sys, plan->h_rpanel_sys.data(), plan->h_rpanel_sys.size() * 4,
+                              cudaMemcpyHostToDevice, s));
+    CHEB_CUDA(cudaMemcpyAsync(plan->d_sys_rpanel, plan->h_sys_rpanel.data(), plan->h_sys_rpanel.size() * 4,
+                              cudaMemcpyHostToDevice, s));
     // The host vectors are read by the async copies: finish them before returning.
     CHEB_CUDA(cudaStreamSynchronize(s));
     plan->bound = true;
@@ -160,6 +258,15 @@ extern "C" int cheb_plan_info(const cheb_plan *plan, int64_t *n_panels, int32_t 
     if (n_panels) *n_panels = plan->n_panels;
     if (panel_width) *panel_width = plan->P;
     if (max_union) *max_union = plan->max_union;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_resident_info(const cheb_plan *plan, int64_t *n_panels, int32_t *max_union,
+                                       int32_t *max_blocks) {
+    if (!plan) return fail(CHEB_ERR_INVALID, "cheb_plan_resident_info: NULL plan");
+    if (n_panels) *n_panels = plan->n_rpanels;
+    if (max_union) *max_union = plan->max_union_res;
+    if (max_blocks) *max_blocks = plan->max_nblk_res;
     return CHEB_OK;
 }
 

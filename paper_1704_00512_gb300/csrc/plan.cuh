@@ -23,11 +23,24 @@ struct cheb_plan {
     int32_t ucap = 0;       // union rows that fit in shared memory
     std::vector<int32_t> h_tperm;   // slot of (J,I) for each slot (I,J)
     std::vector<int32_t> h_panels;  // pairs (first column, column count)
+    // panels of the resident kernel (whole expansion per thread block); they
+    // never straddle two systems of a block-diagonal batch
+    int32_t nsys = 1;
+    std::vector<int64_t> h_sys_col;     // first block column of each system (+ end)
+    std::vector<int32_t> h_rpanels;     // pairs (first column, column count)
+    std::vector<int32_t> h_rpanel_sys;  // system of each resident panel
+    std::vector<int32_t> h_sys_rpanel;  // first resident panel of each system (+ end)
+    int64_t n_rpanels = 0;
+    int32_t max_union_res = 0;  // largest union of row lists over a resident panel
+    int32_t max_nblk_res = 0;   // most blocks held by a resident panel
     // device copies after cheb_plan_bind
     bool bound = false;
     int32_t *d_tperm = nullptr;
     int32_t *d_panels = nullptr;
     int32_t *d_counter = nullptr;  // grid-completion counter used by the step kernel
+    int32_t *d_rpanels = nullptr;
+    int32_t *d_rpanel_sys = nullptr;
+    int32_t *d_sys_rpanel = nullptr;
     size_t ws_bytes = 0;
 };
 
@@ -64,6 +77,42 @@ __host__ __device__ inline StepLayout step_layout(int64_t nw, int64_t ucap, int 
     o = (o + 15) / 16 * 16;
     L.off_red = o;
     o += 128 * 8;  // per-warp moment partials (<= 32 warps x 4)
+    L.total = o;
+    return L;
+}
+
+// Shared-memory layout of the resident kernel: the union bookkeeping of the
+// panel, the global slot of each of its nblk blocks, and two nblk-block buffers
+// (T_k and T_{k-1} / T_{k+1}) that stay in shared memory for the whole expansion.
+struct ResLayout {
+    size_t off_bits, off_ulist, off_pos, off_gslot, off_wl, off_x, off_y, off_red, total;
+};
+
+__host__ __device__ inline ResLayout res_layout(int64_t nw, int64_t ucap, int64_t bcap, int P, int esz, int nwarps) {
+    ResLayout L;
+    size_t o = 0;
+    L.off_bits = o;
+    o += (size_t)nw * 8;
+    o = (o + 15) / 16 * 16;
+    L.off_ulist = o;
+    o += (size_t)ucap * 4;
+    o = (o + 15) / 16 * 16;
+    L.off_pos = o;
+    o += (size_t)ucap * P * 2;
+    o = (o + 15) / 16 * 16;
+    L.off_gslot = o;
+    o += (size_t)bcap * 4;
+    o = (o + 15) / 16 * 16;
+    L.off_wl = o;
+    o += (size_t)nwarps * 64 * 8;
+    o = (o + 127) / 128 * 128;
+    const size_t xb = ((size_t)bcap * BB * esz + 127) / 128 * 128;
+    L.off_x = o;
+    o += xb;
+    L.off_y = o;
+    o += xb;
+    L.off_red = o;
+    o += 128 * 8;
     L.total = o;
     return L;
 }

@@ -335,3 +335,99 @@ def test_every_tile_shape_matches(prec):
         for j in range(nf):
             assert relF(acc[j].cpu().numpy(), ex.acc[j].vals) < tol, (tile, j)
         assert relF(g.cpu().numpy(), ex.g) < tol
+
+
+def test_resident_and_stepwise_expansions_agree_with_oracle():
+    n, nf = 48, 3
+    s, H, P_out, e0, e1, Ht, coeffs, G = _expand_case(180, 5.0, 3.0, 31, n, nf)
+    ex = ref.chebyshev_expand(Ht, P_out, coeffs, G=G)
+    dP = dbsr(P_out.row_ptr, P_out.col_idx)
+    dHt = dbsr(Ht.row_ptr, Ht.col_idx, Ht.vals)
+    for prec, tol in ((cg.F64, 1e-10), (cg.F32, 1e-5)):
+        plan = cg.Plan(dP, prec)
+        outs = {}
+        for stepwise in (False, True):
+            acc = [torch.zeros((P_out.nnzb, 4, 4), dtype=torch.float64, device=DEV) for _ in range(nf)]
+            t = torch.zeros(n, dtype=torch.float64, device=DEV)
+            g = torch.zeros(n, dtype=torch.float64, device=DEV)
+            cg.expand(plan, dHt, n, torch.as_tensor(coeffs, device=DEV), acc, moments=t,
+                      G=torch.as_tensor(G.vals, device=DEV), gmoments=g, precision=prec, stepwise=stepwise)
+            for j in range(nf):
+                assert relF(acc[j].cpu().numpy(), ex.acc[j].vals) < tol
+            assert relF(t.cpu().numpy(), ex.t) < tol and relF(g.cpu().numpy(), ex.g) < tol
+            outs[stepwise] = acc[0].cpu().numpy()
+        # two independent kernels, same arithmetic up to summation order
+        assert relF(outs[False], outs[True]) < (1e-12 if prec == cg.F64 else 1e-5)
+
+
+def _block_diag(systems, r_buf):
+    """Concatenate systems block-diagonally: (P_H, S, H, P_out, row starts)."""
+    rps, cis, Ss, Hs, orps, ocis, starts = [], [], [], [], [], [], [0]
+    off = 0
+    boff = 0
+    oboff = 0
+    for s in systems:
+        rp, ci = ref.pattern(s.xyz, s.L, s.r_cut + r_buf)
+        rps.append(s.row_ptr[:-1] + boff)
+        cis.append(s.col_idx + off)
+        Ss.append(s.S)
+        Hs.append(s.H)
+        orps.append(rp[:-1] + oboff)
+        ocis.append(ci + off)
+        off += s.n_atoms
+        boff += s.nnzb
+        oboff += len(ci)
+        starts.append(off)
+    rp = np.concatenate(rps + [[boff]]).astype(np.int64)
+    orp = np.concatenate(orps + [[oboff]]).astype(np.int64)
+    return (rp, np.concatenate(cis).astype(np.int32), np.concatenate(Ss), np.concatenate(Hs), orp,
+            np.concatenate(ocis).astype(np.int32), starts)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_batched_expansion_matches_per_system_oracle(prec):
+    systems = [synth.make_system(na, 4.0, seed) for na, seed in ((40, 1), (90, 2), (25, 3))]
+    rp, ci, S, H, orp, oci, starts = _block_diag(systems, 2.0)
+    rng = np.random.default_rng(4)
+    ns = [30, 45, 20]
+    nf = 2
+    kmax = max(ns)
+    bounds, Hts = [], []
+    for s in systems:
+        w = np.linalg.eigvalsh(synth.to_dense(s.row_ptr, s.col_idx, s.H))
+        bounds.append((w[0] - 0.1, w[-1] + 0.1))
+    # scale each system's block range of H with its own bounds
+    Ht_vals = np.empty_like(H)
+    bo = 0
+    for s, (e0, e1) in zip(systems, bounds):
+        Ht_vals[bo:bo + s.nnzb] = ref.scale(ref.Bsr(s.row_ptr, s.col_idx, s.H), e0, e1).vals
+        bo += s.nnzb
+    coeffs = np.zeros((len(systems), nf, kmax))
+    for i, n in enumerate(ns):
+        coeffs[i, :, :n] = rng.normal(size=(nf, n)) / (1.0 + np.arange(n)) ** 1.5
+    Gv = rng.normal(size=(len(oci), 4, 4))
+    dP = dbsr(orp, oci)
+    plan = cg.BatchedPlan(dP, starts, prec)
+    assert cg.plan_resident_info(plan)[0] >= len(systems)
+    dHt = dbsr(rp, ci, Ht_vals)
+    acc = [torch.zeros((len(oci), 4, 4), dtype=torch.float64, device=DEV) for _ in range(nf)]
+    t = torch.zeros((len(systems), kmax), dtype=torch.float64, device=DEV)
+    g = torch.zeros((len(systems), kmax), dtype=torch.float64, device=DEV)
+    cg.expand_batched(plan, dHt, kmax, torch.tensor(ns, dtype=torch.int32, device=DEV),
+                      torch.as_tensor(coeffs.reshape(-1), device=DEV),
+                      torch.tensor([i * nf * kmax for i in range(len(systems))], dtype=torch.int64, device=DEV),
+                      kmax, acc, moments=t, G=torch.as_tensor(Gv, device=DEV), gmoments=g, moment_stride=kmax,
+                      precision=prec)
+    tol = 1e-10 if prec == cg.F64 else 1e-5
+    ob = 0
+    for i, s in enumerate(systems):
+        rpo, cio = ref.pattern(s.xyz, s.L, s.r_cut + 2.0)
+        Po = ref.Bsr(rpo, cio, None)
+        Hti = ref.Bsr(s.row_ptr, s.col_idx, Ht_vals[sum(x.nnzb for x in systems[:i]):][:s.nnzb])
+        Gi = Po.with_vals(Gv[ob:ob + len(cio)])
+        ex = ref.chebyshev_expand(Hti, Po, coeffs[i, :, :ns[i]], G=Gi)
+        for j in range(nf):
+            assert relF(acc[j][ob:ob + len(cio)].cpu().numpy(), ex.acc[j].vals) < tol
+        assert relF(t[i, :ns[i]].cpu().numpy(), ex.t) < tol
+        assert relF(g[i, :ns[i]].cpu().numpy(), ex.g) < tol
+        ob += len(cio)
