@@ -317,6 +317,49 @@ int cheb_mu_search(const double *gmoments, int32_t n_terms, double emin, double 
 int cheb_newton_schulz(const cheb_plan *plan, const cheb_bsr *S, const double *X0, double *X1,
                        double *tmp, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * out = sum_{i<n} weights[i] * x[i], elementwise over len doubles (n <= 8;
+ * weights: host array; x: host array of device pointers; out may alias one of
+ * them).  Used to interpolate F(mu) between accumulators taken at several mu
+ * of one expansion.  Asynchronous.
+ */
+int cheb_lincomb(int32_t n, const double *weights, const double *const *x, int64_t len, double *out,
+                 void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned mu proposal (not in the paper).  A 35 -> 128 -> 128 -> 2 ReLU network
+ * in FP32 maps low-order moments of the scaled operator, its bounds and the
+ * filling to a guess of the scaled Fermi level (output 0) and the log of a
+ * bracket half-width in scaled units (output 1).  The plain bisection stays the
+ * judge: it runs on the moments of the full expansion, and a mu outside the
+ * proposed bracket falls back to a second expansion.
+ * Parameters: one flat FP32 vector of cheb_mlp_param_count() = 21378 values,
+ * W1[128][35], b1[128], W2[128][128], b2[128], W3[2][128], b3[2].
+ *   forward: X device float[batch][35] -> out float[batch][2]; act (device
+ *     float[batch*256]) receives the two hidden pre-activations.
+ *   loss: with d = (out0 - xstar)/scale and w = exp(out1)/scale (scale =
+ *     sigma*kT per sample), L = huber(d) + relu(|d| - w) + 0.01 w, mean over
+ *     the batch into *loss (device double, may be NULL); dout = dL/dout.
+ *   backward: grad (device float[param_count]) of sum(dout * out); ws device
+ *     float[batch*256].
+ *   adam: one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step t >= 1).
+ *   features: the 35 inputs from t_k = Tr T_k (device double[32]): t_k/n_rows,
+ *     emin/10, emax/10, N_e/n_rows -> device float[35].
+ * All asynchronous; reductions over the batch are sequential per thread
+ * (reproducible).
+ */
+int cheb_mlp_param_count(void);
+int cheb_mlp_forward(const float *theta, const float *X, int32_t batch, float *act, float *out,
+                     void *stream);
+int cheb_mlp_loss(const float *out, const float *xstar, const float *scale, int32_t batch,
+                  float *dout, double *loss, void *stream);
+int cheb_mlp_backward(const float *theta, const float *X, int32_t batch, const float *act,
+                      const float *dout, float *grad, float *ws, void *stream);
+int cheb_mlp_adam(float *theta, const float *grad, float *m, float *v, int32_t t, float lr,
+                  void *stream);
+int cheb_mlp_features(const double *moments, int64_t n_rows, double emin, double emax, double N_e,
+                      float *features, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

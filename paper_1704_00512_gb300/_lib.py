@@ -29,7 +29,8 @@ EXPORTS = [
     "cheb_plan_destroy", "cheb_scale", "cheb_bounds_workspace_size", "cheb_bounds",
     "cheb_coeffs_workspace_size", "cheb_coeffs", "cheb_expand_workspace_size", "cheb_expand",
     "cheb_expand_stepwise_workspace_size", "cheb_expand_stepwise", "cheb_plan_create_batched",
-    "cheb_plan_resident_info", "cheb_expand_batched",
+    "cheb_plan_resident_info", "cheb_expand_batched", "cheb_lincomb", "cheb_mlp_param_count",
+    "cheb_mlp_forward", "cheb_mlp_loss", "cheb_mlp_backward", "cheb_mlp_adam", "cheb_mlp_features",
     "cheb_masked_product", "cheb_transpose", "cheb_restrict", "cheb_trace_workspace_size", "cheb_trace",
     "cheb_penalty_trace", "cheb_mu_search", "cheb_newton_schulz",
 ]
@@ -88,6 +89,13 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
         "cheb_plan_create_batched": ([P(CBsr), i32, i32, i32, P(i64), P(p), P(sz), p], i32),
         "cheb_plan_resident_info": ([p, P(i64), P(i32), P(i32)], i32),
         "cheb_expand_batched": ([p, P(CBsr), i32, p, p, p, i32, i32, P(p), p, p, p, i32, i32, p, sz, p], i32),
+        "cheb_lincomb": ([i32, P(dbl), P(p), i64, p, p], i32),
+        "cheb_mlp_param_count": ([], i32),
+        "cheb_mlp_forward": ([p, p, i32, p, p, p], i32),
+        "cheb_mlp_loss": ([p, p, p, i32, p, p, p], i32),
+        "cheb_mlp_backward": ([p, p, i32, p, p, p, p, p], i32),
+        "cheb_mlp_adam": ([p, p, p, p, i32, ctypes.c_float, p], i32),
+        "cheb_mlp_features": ([p, i64, dbl, dbl, dbl, p, p], i32),
         "cheb_masked_product": ([p, P(CBsr), p, dbl, p, dbl, p, p], i32),
         "cheb_transpose": ([p, p, p, p], i32),
         "cheb_restrict": ([P(CBsr), P(CBsr), p, p], i32),
@@ -415,3 +423,45 @@ def newton_schulz(plan: Plan, S: Bsr, X0: torch.Tensor, X1: torch.Tensor, tmp: t
     _check(load().cheb_newton_schulz(plan.handle, ctypes.byref(cb), _ptr(X0), _ptr(X1), _ptr(tmp),
                                      _stream(stream)))
     return X1
+
+
+def lincomb(weights, xs: list[torch.Tensor], out: torch.Tensor, stream=None) -> torch.Tensor:
+    """cheb_lincomb: out = sum_i weights[i] * xs[i]."""
+    n = len(xs)
+    w = (ctypes.c_double * n)(*[float(v) for v in weights])
+    arr = (ctypes.c_void_p * n)(*[t.data_ptr() for t in xs])
+    _check(load().cheb_lincomb(n, w, arr, out.numel(), _ptr(out), _stream(stream)))
+    return out
+
+
+def mlp_param_count() -> int:
+    return int(load().cheb_mlp_param_count())
+
+
+def mlp_forward(theta: torch.Tensor, X: torch.Tensor, act: torch.Tensor, out: torch.Tensor, stream=None):
+    _check(load().cheb_mlp_forward(_ptr(theta), _ptr(X), X.shape[0], _ptr(act), _ptr(out), _stream(stream)))
+    return out
+
+
+def mlp_loss(out: torch.Tensor, xstar: torch.Tensor, scale: torch.Tensor, dout: torch.Tensor,
+             loss: torch.Tensor | None = None, stream=None):
+    _check(load().cheb_mlp_loss(_ptr(out), _ptr(xstar), _ptr(scale), out.shape[0], _ptr(dout), _ptr(loss),
+                                _stream(stream)))
+    return dout
+
+
+def mlp_backward(theta, X, act, dout, grad, ws, stream=None):
+    _check(load().cheb_mlp_backward(_ptr(theta), _ptr(X), X.shape[0], _ptr(act), _ptr(dout), _ptr(grad), _ptr(ws),
+                                    _stream(stream)))
+    return grad
+
+
+def mlp_adam(theta, grad, m, v, t: int, lr: float, stream=None):
+    _check(load().cheb_mlp_adam(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), t, lr, _stream(stream)))
+    return theta
+
+
+def mlp_features(moments: torch.Tensor, n_rows: int, emin: float, emax: float, N_e: float, out: torch.Tensor,
+                 stream=None):
+    _check(load().cheb_mlp_features(_ptr(moments), n_rows, emin, emax, N_e, _ptr(out), _stream(stream)))
+    return out

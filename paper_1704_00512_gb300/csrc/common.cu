@@ -99,6 +99,22 @@ __global__ void k_sum_partials(const double *part, int n, double *out) {
 
 constexpr int TRACE_GRID = 304;
 
+struct LinComb {
+    const double *x[8];
+    double w[8];
+};
+
+// out = sum_i w_i x_i (elementwise)
+__global__ void k_lincomb(LinComb c, int n, int64_t len, double *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < n) s += c.w[j] * c.x[j][i];
+        out[i] = s;
+    }
+}
+
 }  // namespace cheb
 
 using namespace cheb;
@@ -171,4 +187,18 @@ extern "C" int cheb_trace(const cheb_bsr *A, const cheb_bsr *B, double *out, voi
     CHEB_TRY(check_launch("k_trace_partial"));
     k_sum_partials<256><<<1, 256, 0, s>>>(part, TRACE_GRID, out);
     return check_launch("k_sum_partials");
+}
+
+extern "C" int cheb_lincomb(int32_t n, const double *weights, const double *const *x, int64_t len, double *out,
+                            void *stream) {
+    if (n < 1 || n > 8 || !weights || !x || !out || len < 0) return fail(CHEB_ERR_INVALID, "cheb_lincomb: bad arguments");
+    LinComb c{};
+    for (int j = 0; j < n; ++j) {
+        if (!x[j]) return fail(CHEB_ERR_INVALID, "cheb_lincomb: input %d is NULL", j);
+        c.x[j] = x[j];
+        c.w[j] = weights[j];
+    }
+    if (len == 0) return CHEB_OK;
+    k_lincomb<<<1216, 256, 0, as_stream(stream)>>>(c, n, len, out);
+    return check_launch("k_lincomb");
 }

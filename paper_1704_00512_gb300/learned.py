@@ -1,0 +1,181 @@
+"""Learned mu proposal: training data from the method, training with the library's
+MLP kernels, and the one-pass solve it enables.  (Not in the paper.)
+
+The plain FOE (solve.foe) needs two expansions: one to collect the trace
+functional g_k for the bisection on Tr(F(mu) S) = N_e, and one to accumulate
+F at the mu it finds.  A proposal (mu_hat, h) lets one expansion carry both:
+g_k plus n_mu accumulators at the Chebyshev nodes mu_i of [mu_hat - h,
+mu_hat + h].  The bisection on g stays the judge; if its mu* lies inside the
+bracket, F(mu*) is the Lagrange interpolant of the n_mu accumulators (F is
+analytic in mu with its nearest singularities about pi*kT from the real axis,
+so for h well below kT the interpolation error is ~(h / (2 pi kT))^n_mu);
+otherwise a second expansion at mu* is run (the fallback).
+
+Every numerical step runs in libcheb.so; this module sequences calls.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from . import solve
+
+N_IN = 35
+N_MOM = 32
+
+
+@dataclasses.dataclass
+class Instance:
+    features: np.ndarray  # [35]
+    xstar: float          # sigma (mu* - tau), the scaled Fermi level
+    scale: float          # sigma * kT
+    kT: float
+    bounds: tuple[float, float]
+    mu: float
+    n_terms: int
+
+
+def prepare(pb: solve.Problem, tol_S: float = 1e-10, lanczos_k: int = 40):
+    """S^-1/2, H', bounds of H', scaled H~' and the trace functional G (as in solve.foe)."""
+    pw = solve.powers(pb, exponents=(-0.5,), tol=tol_S, precision=L.F64)
+    A = pw["acc"][0]
+    Hp = solve.orthogonalise(pb, A)
+    e0, e1, _ = L.bounds(Hp, lanczos_k)
+    Hpt = Hp.with_vals(L.scale(Hp, e0, e1))
+    G = solve.trace_functional(pb, A)
+    return A, Hpt, (e0, e1), G
+
+
+def moments32(pb: solve.Problem, Hpt: L.Bsr) -> torch.Tensor:
+    """t_k = Tr T_k for k < 32 (a 32-term expansion with no accumulators)."""
+    t = torch.zeros(N_MOM, dtype=torch.float64, device=pb.device)
+    L.expand(pb.planX, Hpt, N_MOM, None, [], moments=t, precision=pb.precision)
+    return t
+
+
+def features(pb: solve.Problem, t32: torch.Tensor, bounds, N_e: float) -> torch.Tensor:
+    f = torch.empty(N_IN, dtype=torch.float32, device=pb.device)
+    return L.mlp_features(t32, pb.n_rows, bounds[0], bounds[1], N_e, f)
+
+
+def label_instance(sysm, r_buf: float, kT: float, N_e: float, device, tol: float = 1e-6,
+                   precision: int = L.F32) -> Instance:
+    """Features and the bisection's mu* (the label) for one generated system."""
+    pb = solve.problem_from_system(sysm, r_buf, device, precision)
+    A, Hpt, (e0, e1), G = prepare(pb)
+    n, _ = L.coeffs([{"kind": L.FERMI, "mu": 0.5 * (e0 + e1), "kT": kT}], e0, e1, tol, 16384, device=pb.device)
+    t = torch.zeros(n, dtype=torch.float64, device=pb.device)
+    g = torch.zeros(n, dtype=torch.float64, device=pb.device)
+    L.expand(pb.planX, Hpt, n, None, [], moments=t, G=G, gmoments=g, precision=precision)
+    r = L.decode_mu_result(L.mu_search(g, n, e0, e1, L.FERMI, kT, N_e, 1e-6 * N_e))
+    f = features(pb, t[:N_MOM].contiguous(), (e0, e1), N_e).cpu().numpy()
+    sigma, tau = 2.0 / (e1 - e0), 0.5 * (e0 + e1)
+    return Instance(f, sigma * (r["mu"] - tau), sigma * kT, kT, (e0, e1), r["mu"], n)
+
+
+class Proposal:
+    """The network's parameters on the device plus training state."""
+
+    def __init__(self, theta0: np.ndarray, device):
+        self.device = torch.device(device)
+        self.theta = torch.as_tensor(theta0, dtype=torch.float32, device=self.device).contiguous()
+        self.m = torch.zeros_like(self.theta)
+        self.v = torch.zeros_like(self.theta)
+        self.t = 0
+
+    @staticmethod
+    def xavier(seed: int) -> np.ndarray:
+        """Xavier-uniform weights, zero biases (numpy rng; the caller's random numbers)."""
+        rng = np.random.default_rng(seed)
+        parts = []
+        for nout, nin in ((128, 35), (128, 128), (2, 128)):
+            lim = math.sqrt(6.0 / (nin + nout))
+            parts.append(rng.uniform(-lim, lim, size=nout * nin))
+            parts.append(np.zeros(nout))
+        return np.concatenate(parts)
+
+    def forward(self, X: torch.Tensor) -> torch.Tensor:
+        act = torch.empty(X.shape[0] * 256, dtype=torch.float32, device=self.device)
+        out = torch.empty((X.shape[0], 2), dtype=torch.float32, device=self.device)
+        L.mlp_forward(self.theta, X, act, out)
+        return out
+
+    def train(self, X: np.ndarray, xstar: np.ndarray, scale: np.ndarray, iters: int = 2000, lr: float = 1e-3,
+              log_every: int = 0) -> list[float]:
+        X = torch.as_tensor(X, dtype=torch.float32, device=self.device).contiguous()
+        xs = torch.as_tensor(xstar, dtype=torch.float32, device=self.device).contiguous()
+        sc = torch.as_tensor(scale, dtype=torch.float32, device=self.device).contiguous()
+        B = X.shape[0]
+        act = torch.empty(B * 256, dtype=torch.float32, device=self.device)
+        out = torch.empty((B, 2), dtype=torch.float32, device=self.device)
+        dout = torch.empty_like(out)
+        grad = torch.empty_like(self.theta)
+        ws = torch.empty(B * 256, dtype=torch.float32, device=self.device)
+        loss = torch.zeros(1, dtype=torch.float64, device=self.device)
+        hist = []
+        for it in range(iters):
+            L.mlp_forward(self.theta, X, act, out)
+            L.mlp_loss(out, xs, sc, dout, loss)
+            L.mlp_backward(self.theta, X, act, dout, grad, ws)
+            self.t += 1
+            L.mlp_adam(self.theta, grad, self.m, self.v, self.t, lr)
+            if log_every and (it % log_every == 0 or it == iters - 1):
+                hist.append(float(loss.item()))
+        return hist
+
+
+def chebyshev_nodes(center: float, half: float, n: int) -> list[float]:
+    return [center + half * math.cos(math.pi * (i + 0.5) / n) for i in range(n)]
+
+
+def lagrange_weights(nodes: list[float], x: float) -> list[float]:
+    w = []
+    for i, xi in enumerate(nodes):
+        v = 1.0
+        for j, xj in enumerate(nodes):
+            if j != i:
+                v *= (x - xj) / (xi - xj)
+        w.append(v)
+    return w
+
+
+def foe_learned(pb: solve.Problem, prop: Proposal, kT: float, N_e: float, tol: float = 1e-7, n_mu: int = 4,
+                min_half_kT: float = 0.05, max_half_kT: float = 1.0, tol_N: float | None = None,
+                prepared=None) -> dict:
+    """One-expansion FOE with the learned bracket; bisection judges, fallback on a miss."""
+    A, Hpt, (e0, e1), G = prepare(pb) if prepared is None else prepared
+    sigma, tau = 2.0 / (e1 - e0), 0.5 * (e0 + e1)
+    t32 = moments32(pb, Hpt)
+    X = features(pb, t32, (e0, e1), N_e).view(1, N_IN)
+    o = prop.forward(X).cpu().numpy()[0]
+    mu_hat = float(o[0]) / sigma + tau
+    half = math.exp(float(o[1])) / sigma
+    half = min(max(half, min_half_kT * kT), max_half_kT * kT)
+    mus = chebyshev_nodes(mu_hat, half, n_mu)
+    # same term count as the plain solve (degree chosen at the interval centre)
+    n, _ = L.coeffs([{"kind": L.FERMI, "mu": tau, "kT": kT}], e0, e1, tol, 16384, device=pb.device)
+    _, c = L.coeffs([{"kind": L.FERMI, "mu": m, "kT": kT} for m in mus], e0, e1, 0.0, n, device=pb.device)
+    accs = [pb.zeros_out() for _ in mus]
+    g = torch.zeros(n, dtype=torch.float64, device=pb.device)
+    ws = L.expand(pb.planX, Hpt, n, c, accs, G=G, gmoments=g, precision=pb.precision)
+    if tol_N is None:
+        tol_N = 1e-6 * N_e
+    r = L.decode_mu_result(L.mu_search(g, n, e0, e1, L.FERMI, kT, N_e, tol_N))
+    mu = r["mu"]
+    passes = 1
+    p = pb.zeros_out()
+    if abs(mu - mu_hat) <= half:
+        L.lincomb(lagrange_weights(mus, mu), accs, p)
+    else:
+        _, c2 = L.coeffs([{"kind": L.FERMI, "mu": mu, "kT": kT}], e0, e1, 0.0, n, device=pb.device)
+        L.expand(pb.planX, Hpt, n, c2, [p], precision=pb.precision, ws=ws)
+        passes = 2
+    F = solve.postprocess(pb, A, p)
+    trFS = L.trace(pb.P_out.with_vals(F), pb.S)
+    return {"F": F, "p": p, "mu": mu, "mu_hat": mu_hat, "half": half, "passes": passes, "n_terms": n,
+            "mu_result": r, "trace_FS": trFS, "bounds_H": (e0, e1)}

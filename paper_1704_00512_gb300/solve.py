@@ -137,7 +137,7 @@ def postprocess(pb: Problem, A: torch.Tensor, p: torch.Tensor) -> torch.Tensor:
 def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FERMI, n_max: int = 16384,
         lanczos_k: int = 40, tol_N: float | None = None, bounds_S=None, n_S=None, bounds_H=None, n_H=None,
         max_iter: int = 100, n_mu: int = 1, mu_stencil: float = 0.05, tol_S: float | None = None,
-        timings: dict | None = None) -> dict:
+        stepwise: bool = True, timings: dict | None = None) -> dict:
     """Density matrix F with Tr(F S) = N_e (see the module docstring for the steps)."""
     tm = {} if timings is None else timings
     t0 = time.perf_counter()
@@ -161,7 +161,7 @@ def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FE
     g = torch.zeros(n, dtype=torch.float64, device=pb.device)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
-    ws = L.expand(pb.planX, Hpt, n, None, [], moments=t, G=G, gmoments=g, precision=pb.precision)
+    ws = L.expand(pb.planX, Hpt, n, None, [], moments=t, G=G, gmoments=g, precision=pb.precision, stepwise=stepwise)
     ev[1].record()
     if tol_N is None:
         tol_N = 1e-9 * N_e if pb.precision == L.F64 else 1e-6 * N_e
@@ -174,7 +174,7 @@ def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FE
     _, c = L.coeffs([{"kind": kind, "mu": m, "kT": kT} for m in mus], e0, e1, 0.0, n, device=pb.device)
     accs = [pb.zeros_out() for _ in mus]
     ev[2].record()
-    L.expand(pb.planX, Hpt, n, c, accs, precision=pb.precision, ws=ws)
+    L.expand(pb.planX, Hpt, n, c, accs, precision=pb.precision, ws=ws, stepwise=stepwise)
     ev[3].record()
     p = accs[0]
     F = postprocess(pb, A, p)
