@@ -43,6 +43,10 @@ WORKLOADS = {
     # The same solve on 3,000 atoms (12,000 rows): profiling stand-in for the launch list.
     "foe_mixed_12k": dict(n_atoms=3000, r_c=10.0, r_buf=4.0, kT=0.005, N_e=6000.0, tol=1e-7, tol_S=1e-10,
                           precision="f32", n_mu=4),
+    # Same 12,000-row system at kT = 0.05 (about 10x fewer terms): keeps a per-launch
+    # profiler capture of a whole solve short.
+    "foe_mixed_12k_kT05": dict(n_atoms=3000, r_c=10.0, r_buf=4.0, kT=0.05, N_e=6000.0, tol=1e-7, tol_S=1e-10,
+                               precision="f32", n_mu=4),
     # The plain FP64 density matrix: 200 atoms x 4, 8 bohr cutoff, kT = 0.01, N_e = 400.
     "foe_fp64_800": dict(n_atoms=200, r_c=8.0, r_buf=4.0, kT=0.01, N_e=400.0, tol=1e-10, tol_S=1e-10,
                          precision="f64", n_mu=1),
@@ -63,13 +67,16 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
     NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, enabled: bool = True):
         self.idx = gpu_index
+        self.enabled = enabled
         self.proc = None
         self.lines: list[str] = []
         self.th = None
 
     def start(self):
+        if not self.enabled:
+            return
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -86,7 +93,8 @@ class ClockSampler:
 
     def stop(self) -> dict:
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            why = "not sampled (--no-clocks)" if not self.enabled else "nvidia-smi unavailable"
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [why]}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -182,7 +190,7 @@ def run_cheb(args, rank: int, world: int, local: int):
             f"TrFS={out['trace_FS'].item():.6f}")
 
     # ---- device-resident timed region
-    clk = ClockSampler(local)
+    clk = ClockSampler(local, enabled=not args.no_clocks)
     pass_ms = []
     if world > 1:
         dist.barrier()
@@ -375,6 +383,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1, help="solves in the end-to-end (host buffers) loop")
+    ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (e.g. under a profiler)")
     args = ap.parse_args()
     if args.warmup < 3:
         log("note: fewer than 3 warm-up steps")

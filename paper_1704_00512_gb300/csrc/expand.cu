@@ -137,16 +137,18 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
         const int q = lane % P, kg = lane / P;
         const unsigned lt = (1u << lane) - 1u;
         int2 *wl = wlist + warp * 64;
-        T *hb = hbuf + (size_t)warp * 2 * 32 * BB;  // two batches of 32 staged blocks
+        // two batches of 32 staged blocks, chunks XOR-swizzled like the panel blocks
+        unsigned char *hb = reinterpret_cast<unsigned char *>(hbuf + (size_t)warp * 2 * 32 * BB);
         int *bs = bslot + warp * 64;                 // union slots of the staged blocks
         auto issue = [&](int buf, int n) {
             if (lane < n) {
                 const int2 e = wl[lane];
                 bs[buf * 32 + lane] = e.y;
                 const T *src = a.Lv + (int64_t)e.x * BB;
-                T *dst = hb + ((size_t)buf * 32 + lane) * BB;
+                const int b = buf * 32 + lane;
 #pragma unroll
-                for (int c = 0; c < (int)(BB * sizeof(T) / 16); ++c) cp_async16(dst + c * (16 / sizeof(T)), src + c * (16 / sizeof(T)));
+                for (int c = 0; c < (int)(BB * sizeof(T) / 16); ++c)
+                    cp_async16(hb + rchunk<T>(b, c), src + c * (16 / sizeof(T)));
             }
             cp_async_commit();
         };
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
                 const int e = u * KG + kg;
                 if (e >= n) continue;
                 T h[16];
-                lds16<T>(h, hb + ((size_t)buf * 32 + e) * BB);
+                r_ld<T>(h, hb, buf * 32 + e);
                 const int s2 = bs[buf * 32 + e];
                 const T *xs = X + s2 * (BB * P) + 4 * q;
                 const int sw = s2 & 1;
@@ -171,15 +173,35 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
                 }
             }
         };
+        // Row bounds and the first 32 column indices are fetched one row ahead
+        // (the bounds two rows ahead) so their latency overlaps the current row.
+        int64_t ca0 = 0, ca1 = 0, na0 = 0, na1 = 0;
+        if (warp < nu) {
+            const int I0 = ulist[warp];
+            ca0 = a.Lrp[I0];
+            ca1 = a.Lrp[I0 + 1];
+        }
+        int Kc = (warp < nu && ca0 + lane < ca1) ? a.Lci[ca0 + lane] : -1;
+        if (warp + NW < nu) {
+            const int I1 = ulist[warp + NW];
+            na0 = a.Lrp[I1];
+            na1 = a.Lrp[I1 + 1];
+        }
         for (int s = warp; s < nu; s += NW) {
-            const int I = ulist[s];
-            const int64_t a0 = a.Lrp[I], a1 = a.Lrp[I + 1];
+            const int Kn = (s + NW < nu && na0 + lane < na1) ? a.Lci[na0 + lane] : -1;
+            int64_t ma0 = 0, ma1 = 0;
+            if (s + 2 * NW < nu) {
+                const int I2 = ulist[s + 2 * NW];
+                ma0 = a.Lrp[I2];
+                ma1 = a.Lrp[I2 + 1];
+            }
+            const int64_t a0 = ca0, a1 = ca1;
             T acc[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) acc[i] = T(0);
             int pending = 0, inflight = -1, n_inflight = 0, nb = 0;
             int64_t base = a0;
-            int Knext = (a0 + lane < a1) ? a.Lci[a0 + lane] : -1;
+            int Knext = Kc;
             while (true) {
                 if (base < a1) {
                     const int K = Knext;
@@ -233,6 +255,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
                         if (i / EPL == kg) a.C[slot + i] = acc[i];
                 }
             }
+            ca0 = na0;
+            ca1 = na1;
+            Kc = Kn;
+            na0 = ma0;
+            na1 = ma1;
         }
     }
     __syncthreads();
@@ -281,14 +308,18 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
         double yd[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) yd[c] = (double)y[c];
+        // all accumulator rows are loaded before any is written back, so their
+        // loads are in flight together
+        double av[MAX_F][4];
+#pragma unroll
+        for (int f = 0; f < MAX_F; ++f)
+            if (f < a.nf) Vec4<double>::ld(av[f], a.acc[f] + idx);
 #pragma unroll
         for (int f = 0; f < MAX_F; ++f) {
             if (f < a.nf) {
-                double v[4];
-                Vec4<double>::ld(v, a.acc[f] + idx);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) v[c] += coefv[f] * yd[c];
-                Vec4<double>::st(a.acc[f] + idx, v);
+                for (int c = 0; c < 4; ++c) av[f][c] += coefv[f] * yd[c];
+                Vec4<double>::st(a.acc[f] + idx, av[f]);
             }
         }
         if (a.G) {

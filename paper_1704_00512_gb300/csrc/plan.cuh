@@ -122,7 +122,7 @@ __host__ __device__ inline ResLayout res_layout(int64_t nw, int64_t ucap, int64_
 struct TileCfg {
     int P, NW, MINB;
 };
-constexpr TileCfg TILES_F32[] = {{4, 8, 1}, {4, 16, 1}, {4, 12, 1}, {2, 8, 2}, {2, 4, 3}, {1, 8, 3}};
+constexpr TileCfg TILES_F32[] = {{4, 16, 1}, {4, 8, 1}, {4, 12, 1}, {2, 8, 2}, {2, 4, 3}, {1, 8, 3}};
 constexpr TileCfg TILES_F64[] = {{2, 8, 1}, {2, 4, 2}, {1, 8, 2}, {1, 4, 3}, {2, 16, 1}};
 constexpr int N_TILES_F32 = sizeof(TILES_F32) / sizeof(TileCfg);
 constexpr int N_TILES_F64 = sizeof(TILES_F64) / sizeof(TileCfg);

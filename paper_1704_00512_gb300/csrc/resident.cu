@@ -53,38 +53,6 @@ struct ResArgs {
     int32_t kmax;
 };
 
-// Byte offset of 16-byte chunk c of panel block b (XOR-swizzled inside its
-// 128-byte line so 32 lanes reading chunk c of 32 blocks spread over the banks).
-template <typename T>
-__device__ __forceinline__ int rchunk(int b, int c);
-template <>
-__device__ __forceinline__ int rchunk<float>(int b, int c) {
-    const int line = b >> 1;
-    return line * 128 + ((((b & 1) << 2) | c) ^ (line & 7)) * 16;
-}
-template <>
-__device__ __forceinline__ int rchunk<double>(int b, int c) {
-    return b * 128 + ((c ^ b) & 7) * 16;
-}
-
-template <typename T>
-__device__ __forceinline__ void r_ld(T (&x)[16], const unsigned char *B, int b);
-template <>
-__device__ __forceinline__ void r_ld<float>(float (&x)[16], const unsigned char *B, int b) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const float4 v = *reinterpret_cast<const float4 *>(B + rchunk<float>(b, c));
-        x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
-    }
-}
-template <>
-__device__ __forceinline__ void r_ld<double>(double (&x)[16], const unsigned char *B, int b) {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const double2 v = *reinterpret_cast<const double2 *>(B + rchunk<double>(b, c));
-        x[2 * c] = v.x; x[2 * c + 1] = v.y;
-    }
-}
 template <typename T>
 __device__ __forceinline__ void r_st(unsigned char *B, int b, const T (&x)[16]);
 template <>
