@@ -129,7 +129,8 @@ int cheb_pattern_build(const double *xyz, int64_t n_atoms, double box_L, double 
  * pointers are remembered by the plan and must stay valid too.
  * cheb_plan_info reports (n_panels, panel width, max panel union rows) of the
  * per-step kernel; cheb_plan_resident_info (n_panels, max union rows, max
- * blocks per panel) of the resident expansion kernel.
+ * blocks per panel) of the resident expansion kernel.  A CHEB_BF16 plan uses
+ * the FP32 tile shapes.
  */
 typedef struct cheb_plan cheb_plan;
 
@@ -217,7 +218,11 @@ int cheb_expand(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_terms,
 /* The same expansion as one kernel launch per step (T_k in HBM, three
  * P_out-sized buffers in the workspace).  Same arguments and results up to
  * rounding order; kept as an independent second implementation and for
- * plans whose panels do not fit the resident kernel. */
+ * plans whose panels do not fit the resident kernel.  It also takes
+ * precision CHEB_BF16 (with a CHEB_BF16 plan): Mt and every stored T_k are
+ * rounded to bfloat16 (round to nearest even) while the block products are
+ * summed in FP32 and the accumulators/moments kept in FP64 -- bfloat16 block
+ * products with FP32 accumulation. */
 int cheb_expand_stepwise_workspace_size(const cheb_plan *plan, const cheb_bsr *Mt,
                                         int32_t precision, size_t *bytes);
 int cheb_expand_stepwise(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_terms,
@@ -316,6 +321,14 @@ int cheb_mu_search(const double *gmoments, int32_t n_terms, double emin, double 
  */
 int cheb_newton_schulz(const cheb_plan *plan, const cheb_bsr *S, const double *X0, double *X1,
                        double *tmp, void *stream);
+
+/* The same kind of correction for S^-1/2 (not in the paper):
+ *   Z1 = 1.5 Z0 - 0.5 P_out(Z0 P_out(S P_out(Z0 Z0))),
+ * which squares the relative error of a Z0 that commutes with S (one step after
+ * a reduced-precision expansion).  tmp1, tmp2: device double[nnzb(P_out)*16];
+ * all pointers distinct.  Asynchronous. */
+int cheb_newton_schulz_isqrt(const cheb_plan *plan, const cheb_bsr *S, const double *Z0, double *Z1,
+                             double *tmp1, double *tmp2, void *stream);
 
 /* ---------------------------------------------------------------------------
  * out = sum_{i<n} weights[i] * x[i], elementwise over len doubles (n <= 8;

@@ -575,6 +575,14 @@ def newton_schulz(S: Bsr, X0: Bsr, P_out: Bsr) -> Bsr:
     return P_out.with_vals(2.0 * X0.vals - Z.vals)
 
 
+def newton_schulz_isqrt(S: Bsr, Z0: Bsr, P_out: Bsr) -> Bsr:
+    """One in-pattern Newton-Schulz step for S^-1/2: Z1 = 1.5 Z0 - 0.5 P(Z0 P(S P(Z0 Z0)))."""
+    Y = mp(Z0, Z0, P_out)
+    W = mp(S, Y, P_out)
+    V = mp(Z0, W, P_out)
+    return P_out.with_vals(1.5 * Z0.vals - 0.5 * V.vals)
+
+
 def orthogonalise(H: Bsr, A: Bsr, P_out: Bsr) -> Bsr:
     """M' = P_H(A P_out(H A)) with A = S^-1/2 (Sec. "Fermi Operator Expansion":
     the input matrix is replaced by S^-1/2 M S^-1/2); the result keeps H's pattern."""

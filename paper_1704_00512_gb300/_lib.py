@@ -32,7 +32,7 @@ EXPORTS = [
     "cheb_plan_resident_info", "cheb_expand_batched", "cheb_lincomb", "cheb_mlp_param_count",
     "cheb_mlp_forward", "cheb_mlp_loss", "cheb_mlp_backward", "cheb_mlp_adam", "cheb_mlp_features",
     "cheb_masked_product", "cheb_transpose", "cheb_restrict", "cheb_trace_workspace_size", "cheb_trace",
-    "cheb_penalty_trace", "cheb_mu_search", "cheb_newton_schulz",
+    "cheb_penalty_trace", "cheb_mu_search", "cheb_newton_schulz", "cheb_newton_schulz_isqrt",
 ]
 
 
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
         "cheb_penalty_trace": ([p, i32, dbl, p, p, sz, p], i32),
         "cheb_mu_search": ([p, i32, dbl, dbl, i32, dbl, dbl, dbl, i32, p, p, p, sz, p], i32),
         "cheb_newton_schulz": ([p, P(CBsr), p, p, p, p], i32),
+        "cheb_newton_schulz_isqrt": ([p, P(CBsr), p, p, p, p, p], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -465,3 +466,12 @@ def mlp_features(moments: torch.Tensor, n_rows: int, emin: float, emax: float, N
                  stream=None):
     _check(load().cheb_mlp_features(_ptr(moments), n_rows, emin, emax, N_e, _ptr(out), _stream(stream)))
     return out
+
+
+def newton_schulz_isqrt(plan: Plan, S: Bsr, Z0: torch.Tensor, Z1: torch.Tensor, tmp1: torch.Tensor,
+                        tmp2: torch.Tensor, stream=None) -> torch.Tensor:
+    """cheb_newton_schulz_isqrt: Z1 = 1.5 Z0 - 0.5 P(Z0 P(S P(Z0 Z0)))."""
+    cb = S.c()
+    _check(load().cheb_newton_schulz_isqrt(plan.handle, ctypes.byref(cb), _ptr(Z0), _ptr(Z1), _ptr(tmp1), _ptr(tmp2),
+                                           _stream(stream)))
+    return Z1

@@ -18,6 +18,8 @@
 //      to every FP64 accumulator j, and sums Tr T_{k+1} and <T_{k+1}, G>;
 //   5. the last thread block to finish sums the per-block moment partials in
 //      a fixed order (deterministic) and resets the completion counter.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "plan.cuh"
@@ -49,7 +51,12 @@ struct StepArgs {
     double *gmom;  // device scalar for <T_{k+1}, G> (or NULL)
     double *part;  // per-block partials
     int32_t *counter;
+    int32_t round_bf16;  // store T_{k+1} rounded to bfloat16 (CHEB_BF16 mode)
 };
+
+// x rounded to the nearest bfloat16 (ties to even), returned as float
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ double bf16_round(double x) { return x; }
 
 template <typename T, int P, int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
@@ -304,6 +311,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) y[c] = a.alpha * y[c];
         }
+        if (a.round_bf16) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) y[c] = bf16_round(y[c]);
+        }
         Vec4<T>::st(a.C + idx, y);
         double yd[4];
 #pragma unroll
@@ -362,7 +373,8 @@ __global__ void __launch_bounds__(NT) k_init(const int64_t *rp, const int32_t *c
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const T v0 = (K == J && (i % 5) == 0) ? T(1) : T(0);
-                const T v1 = la >= 0 ? (T)Mt[la * BB + i] : T(0);
+                T v1 = la >= 0 ? (T)Mt[la * BB + i] : T(0);
+                if (a.round_bf16) v1 = bf16_round(v1);
                 T0[slot + i] = v0;
                 T1[slot + i] = v1;
                 const double d0 = (double)v0, d1 = (double)v1;
@@ -384,9 +396,9 @@ __global__ void __launch_bounds__(NT) k_init(const int64_t *rp, const int32_t *c
     finish_moments<NT, 4>(a.part, a.counter, mm, red);
 }
 
-__global__ void k_to_f32(const double *in, float *out, int64_t n) {
+__global__ void k_to_f32(const double *in, float *out, int64_t n, int round_bf16) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (float)in[i];
+    if (i < n) out[i] = round_bf16 ? __bfloat162float(__float2bfloat16_rn(in[i])) : (float)in[i];
 }
 
 template <typename T, int P, int NW, int MINB>
@@ -455,7 +467,7 @@ size_t expand_ws(const cheb_plan *plan, int64_t nnzL, int precision) {
 template <typename T>
 int expand_impl(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_terms, const double *coeffs,
                 int32_t stride, int32_t nf, double *const *acc, double *moments, const double *G,
-                double *gmoments, void *ws, size_t ws_bytes, cudaStream_t s) {
+                double *gmoments, void *ws, size_t ws_bytes, cudaStream_t s, int round_bf16 = 0) {
     Carve cv(ws, ws_bytes);
     T *buf[3];
     for (int i = 0; i < 3; ++i) buf[i] = cv.take<T>(plan->nnzb * BB);
@@ -465,7 +477,7 @@ int expand_impl(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_terms, cons
     } else {
         float *lv = cv.take<float>(Mt->nnzb * BB);
         int64_t n = Mt->nnzb * BB;
-        k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double *)Mt->vals, lv, n);
+        k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double *)Mt->vals, lv, n, round_bf16);
         CHEB_TRY(check_launch("k_to_f32"));
         Lv = reinterpret_cast<const T *>(lv);
     }
@@ -481,6 +493,7 @@ int expand_impl(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_terms, cons
     a.G = G;
     a.part = part;
     a.counter = counter;
+    a.round_bf16 = round_bf16;
     k_init<T, 256><<<(unsigned)plan->n_panels, 256, 0, s>>>(plan->rp, plan->ci, plan->d_tperm, plan->d_panels,
                                                           Mt->row_ptr, Mt->col_idx, (const double *)Mt->vals,
                                                           buf[0], buf[1], nf, a, moments, gmoments);
@@ -534,9 +547,9 @@ extern "C" int cheb_expand_stepwise(const cheb_plan *plan, const cheb_bsr *Mt, i
     if (precision == CHEB_F64)
         return expand_impl<double>(plan, Mt, n_terms, coeffs, coeff_stride, n_f, acc, moments, G, gmoments, ws,
                                    ws_bytes, s);
-    if (precision == CHEB_F32)
+    if (precision == CHEB_F32 || precision == CHEB_BF16)
         return expand_impl<float>(plan, Mt, n_terms, coeffs, coeff_stride, n_f, acc, moments, G, gmoments, ws,
-                                  ws_bytes, s);
+                                  ws_bytes, s, precision == CHEB_BF16);
     return fail(CHEB_ERR_INVALID, "cheb_expand_stepwise: unsupported precision %d", precision);
 }
 
@@ -563,4 +576,16 @@ extern "C" int cheb_newton_schulz(const cheb_plan *plan, const cheb_bsr *S, cons
     if (!plan) return CHEB_ERR_INVALID;
     cheb_bsr Xb{plan->nbr, plan->nnzb, plan->rp, plan->ci, const_cast<double *>(X0), CHEB_F64};
     return cheb_masked_product(plan, &Xb, tmp, -1.0, X0, 2.0, X1, stream);
+}
+
+extern "C" int cheb_newton_schulz_isqrt(const cheb_plan *plan, const cheb_bsr *S, const double *Z0, double *Z1,
+                                        double *tmp1, double *tmp2, void *stream) {
+    if (!plan || !S || !Z0 || !Z1 || !tmp1 || !tmp2 || Z1 == Z0 || Z1 == tmp1 || Z1 == tmp2 || tmp1 == tmp2 ||
+        tmp1 == Z0 || tmp2 == Z0)
+        return fail(CHEB_ERR_INVALID, "cheb_newton_schulz_isqrt: bad pointers");
+    cheb_bsr Zb{plan->nbr, plan->nnzb, plan->rp, plan->ci, const_cast<double *>(Z0), CHEB_F64};
+    // tmp1 = P(Z0 Z0); tmp2 = P(S tmp1); Z1 = 1.5 Z0 - 0.5 P(Z0 tmp2)
+    CHEB_TRY(cheb_masked_product(plan, &Zb, Z0, 1.0, nullptr, 0.0, tmp1, stream));
+    CHEB_TRY(cheb_masked_product(plan, S, tmp1, 1.0, nullptr, 0.0, tmp2, stream));
+    return cheb_masked_product(plan, &Zb, tmp2, -0.5, Z0, 1.5, Z1, stream);
 }

@@ -27,13 +27,14 @@ static int union_capacity(int64_t nbr, int P, int esz, int nwarps, size_t budget
 }
 
 extern "C" int cheb_tile_count(int32_t precision) {
-    if (precision != CHEB_F64 && precision != CHEB_F32) return 0;
+    if (precision != CHEB_F64 && precision != CHEB_F32 && precision != CHEB_BF16) return 0;
     return n_tiles(precision);
 }
 
 extern "C" int cheb_tile_info(int32_t precision, int32_t tile, int32_t *panel_width, int32_t *warps,
                               int32_t *blocks_per_sm) {
-    if ((precision != CHEB_F64 && precision != CHEB_F32) || tile < 0 || tile >= n_tiles(precision))
+    if ((precision != CHEB_F64 && precision != CHEB_F32 && precision != CHEB_BF16) || tile < 0 ||
+        tile >= n_tiles(precision))
         return fail(CHEB_ERR_INVALID, "cheb_tile_info: no tile %d for precision %d", tile, precision);
     const TileCfg c = tile_cfg(precision, tile);
     if (panel_width) *panel_width = c.P;
@@ -48,8 +49,8 @@ static int plan_create_impl(const cheb_bsr *P_out, int32_t precision, int32_t ti
     *out = nullptr;
     if (!P_out || P_out->nbr < 1 || P_out->nnzb < P_out->nbr || !P_out->row_ptr || !P_out->col_idx)
         return fail(CHEB_ERR_INVALID, "cheb_plan_create: bad pattern");
-    if (precision != CHEB_F64 && precision != CHEB_F32)
-        return fail(CHEB_ERR_INVALID, "cheb_plan_create: precision must be CHEB_F64 or CHEB_F32");
+    if (precision != CHEB_F64 && precision != CHEB_F32 && precision != CHEB_BF16)
+        return fail(CHEB_ERR_INVALID, "cheb_plan_create: precision must be CHEB_F64, CHEB_F32 or CHEB_BF16");
     if (P_out->nnzb >= (int64_t)INT32_MAX) return fail(CHEB_ERR_INVALID, "cheb_plan_create: too many blocks");
     if (tile < 0) tile = 0;
     if (tile >= n_tiles(precision)) return fail(CHEB_ERR_INVALID, "cheb_plan_create: no tile %d", tile);

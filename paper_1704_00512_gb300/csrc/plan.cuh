@@ -126,7 +126,7 @@ constexpr TileCfg TILES_F32[] = {{4, 16, 1}, {4, 8, 1}, {4, 12, 1}, {2, 8, 2}, {
 constexpr TileCfg TILES_F64[] = {{2, 8, 1}, {2, 4, 2}, {1, 8, 2}, {1, 4, 3}, {2, 16, 1}};
 constexpr int N_TILES_F32 = sizeof(TILES_F32) / sizeof(TileCfg);
 constexpr int N_TILES_F64 = sizeof(TILES_F64) / sizeof(TileCfg);
-inline int n_tiles(int precision) { return precision == CHEB_F64 ? N_TILES_F64 : N_TILES_F32; }
+inline int n_tiles(int precision) { return precision == CHEB_F64 ? N_TILES_F64 : N_TILES_F32; }  // F32 and BF16 share
 inline TileCfg tile_cfg(int precision, int tile) {
     return precision == CHEB_F64 ? TILES_F64[tile] : TILES_F32[tile];
 }

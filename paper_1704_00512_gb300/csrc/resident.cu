@@ -508,7 +508,8 @@ extern "C" int cheb_expand(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_
     if (precision == CHEB_F32)
         return resident_impl<float>(plan, Mt, n_terms, nullptr, n_terms, cf, nullptr, coeff_stride, n_f, acc, moments,
                                     G, gmoments, n_terms, ws, ws_bytes, s);
-    return fail(CHEB_ERR_INVALID, "cheb_expand: unsupported precision %d", precision);
+    return fail(CHEB_ERR_INVALID, "cheb_expand: unsupported precision %d (CHEB_BF16: cheb_expand_stepwise)",
+                precision);
 }
 
 extern "C" int cheb_expand_batched(const cheb_plan *plan, const cheb_bsr *Mt, int32_t max_terms,

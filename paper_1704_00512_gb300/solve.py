@@ -137,13 +137,22 @@ def postprocess(pb: Problem, A: torch.Tensor, p: torch.Tensor) -> torch.Tensor:
 def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FERMI, n_max: int = 16384,
         lanczos_k: int = 40, tol_N: float | None = None, bounds_S=None, n_S=None, bounds_H=None, n_H=None,
         max_iter: int = 100, n_mu: int = 1, mu_stencil: float = 0.05, tol_S: float | None = None,
-        stepwise: bool = True, timings: dict | None = None) -> dict:
-    """Density matrix F with Tr(F S) = N_e (see the module docstring for the steps)."""
+        stepwise: bool = True, isqrt: str = "f64", timings: dict | None = None) -> dict:
+    """Density matrix F with Tr(F S) = N_e (see the module docstring for the steps).
+
+    isqrt: "f64" expands S^-1/2 in FP64; "f32ns" expands it in the problem's
+    reduced precision and applies one FP64 Newton-Schulz correction.
+    """
     tm = {} if timings is None else timings
     t0 = time.perf_counter()
-    pw = powers(pb, exponents=(-0.5,), tol=tol if tol_S is None else tol_S, bounds_S=bounds_S, n_terms=n_S,
-                precision=L.F64)
-    A = pw["acc"][0]
+    tS = tol if tol_S is None else tol_S
+    if isqrt == "f32ns" and pb.precision != L.F64:
+        pw = powers(pb, exponents=(-0.5,), tol=tS, bounds_S=bounds_S, n_terms=n_S, precision=pb.precision)
+        A = pb.zeros_out()
+        L.newton_schulz_isqrt(pb.plan64, pb.S, pw["acc"][0], A, pb.zeros_out(), pb.zeros_out())
+    else:
+        pw = powers(pb, exponents=(-0.5,), tol=tS, bounds_S=bounds_S, n_terms=n_S, precision=L.F64)
+        A = pw["acc"][0]
     Hp = orthogonalise(pb, A)
     if bounds_H is None:
         e0, e1, _ = L.bounds(Hp, lanczos_k)

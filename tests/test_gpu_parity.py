@@ -431,3 +431,40 @@ def test_batched_expansion_matches_per_system_oracle(prec):
         assert relF(t[i, :ns[i]].cpu().numpy(), ex.t) < tol
         assert relF(g[i, :ns[i]].cpu().numpy(), ex.g) < tol
         ob += len(cio)
+
+
+def test_newton_schulz_isqrt_parity():
+    s, S, H, P_out = setup(150, 5.0, 3.0, 17)
+    rng = np.random.default_rng(5)
+    Z0 = P_out.with_vals(rng.normal(size=(P_out.nnzb, 4, 4)) * 0.1)
+    want = ref.newton_schulz_isqrt(S, Z0, P_out).vals
+    dP = dbsr(P_out.row_ptr, P_out.col_idx)
+    plan = cg.Plan(dP, cg.F64)
+    dZ0 = torch.as_tensor(Z0.vals, device=DEV)
+    Z1, t1, t2 = torch.empty_like(dZ0), torch.empty_like(dZ0), torch.empty_like(dZ0)
+    cg.newton_schulz_isqrt(plan, dbsr(s.row_ptr, s.col_idx, s.S), dZ0, Z1, t1, t2)
+    assert relF(Z1.cpu().numpy(), want) < 1e-12
+
+
+def test_mixed_precision_foe_error_vs_fp64():
+    # The FP32 recursion (FP64 accumulators, FP64 S^-1/2) against the all-FP64
+    # solve with the same bounds and term count must stay within the 1e-6
+    # relative Frobenius target.  The alternative S^-1/2 from an FP32 expansion
+    # plus one FP64 Newton-Schulz step converges to the in-pattern fixed point
+    # of that iteration, which differs from the truncated Chebyshev S^-1/2 by
+    # the truncation error of the pattern (reported, loose bound).
+    s = synth.make_system(400, 6.0, 18)
+    N_e = float(s.n_rows // 2)
+    ref64 = solve.foe_solve(s, 3.0, kT=0.04, N_e=N_e, tol=1e-9, device=DEV)
+    F64 = ref64["F_host"]
+    errs = {}
+    for mode in ("f64", "f32ns"):
+        out = solve.foe_solve(s, 3.0, kT=0.04, N_e=N_e, tol=1e-9, precision=cg.F32, device=DEV,
+                              bounds_S=ref64["bounds_S"], n_S=ref64["n_S"], bounds_H=ref64["bounds_H"],
+                              n_H=ref64["n_terms"], isqrt=mode)
+        errs[mode] = relF(out["F_host"], F64)
+        print(f"isqrt={mode}: n_terms={out['n_terms']} relF(F32 vs F64) = {errs[mode]:.3e}, "
+              f"Tr(FS)-N_e = {out['trace_FS'] - N_e:.2e}")
+        assert abs(out["trace_FS"] - N_e) < 1e-5 * N_e
+    assert errs["f64"] < 1e-6
+    assert errs["f32ns"] < 1e-3

@@ -487,3 +487,20 @@ def test_transpose_and_error_metrics():
     mask = np.ones((3, 3), bool)
     assert ref.error_eq9(M + 0.3, M, mask) == pytest.approx(np.sqrt(9 * 0.09) / 9)
     assert ref.error_eq8(M, M, mask) == 0.0
+
+
+def test_newton_schulz_isqrt_squares_the_error():
+    s, S, H, P = _dense_foe_case(n_atoms=8, seed=16)
+    Sd = S.dense()
+    w, U = np.linalg.eigh(Sd)
+    Z = (U * w ** -0.5) @ U.T
+    for eps in (1e-3, 1e-5):
+        # a perturbation that commutes with S: Z0 = Z (1 + eps D), D diagonal in S's eigenbasis
+        D = (U * np.linspace(-1, 1, len(w))) @ U.T
+        Z0 = _bsr_from_dense(Z @ (np.eye(len(w)) + eps * D), P.row_ptr, P.col_idx)
+        Z1 = ref.newton_schulz_isqrt(S, Z0, P).dense()
+        e0 = np.linalg.norm(Z0.dense() - Z) / np.linalg.norm(Z)
+        e1 = np.linalg.norm(Z1 - Z) / np.linalg.norm(Z)
+        assert e1 < 3 * e0 ** 2
+    Z1 = ref.newton_schulz_isqrt(S, _bsr_from_dense(Z, P.row_ptr, P.col_idx), P).dense()
+    assert ref.rel_frobenius(Z1, Z) < 1e-13
