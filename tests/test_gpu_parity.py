@@ -468,3 +468,20 @@ def test_mixed_precision_foe_error_vs_fp64():
         assert abs(out["trace_FS"] - N_e) < 1e-5 * N_e
     assert errs["f64"] < 1e-6
     assert errs["f32ns"] < 1e-3
+
+
+def test_mixed_precision_error_at_the_bench_degree():
+    # Same kT (0.005 Ha) and fit tolerance (1e-7) as the 40,000-row bench solve,
+    # hence about the same number of terms (~9e3), on a 2,000-row system: the
+    # FP32-recursion F against the all-FP64 F.
+    s = synth.make_system(500, 10.0, 19)
+    N_e = float(s.n_rows // 2)
+    ref64 = solve.foe_solve(s, 4.0, kT=0.005, N_e=N_e, tol=1e-7, tol_S=1e-10, device=DEV)
+    out = solve.foe_solve(s, 4.0, kT=0.005, N_e=N_e, tol=1e-7, tol_S=1e-10, precision=cg.F32, device=DEV,
+                          bounds_S=ref64["bounds_S"], n_S=ref64["n_S"], bounds_H=ref64["bounds_H"],
+                          n_H=ref64["n_terms"])
+    err = relF(out["F_host"], ref64["F_host"])
+    print(f"bench degree: n_terms={out['n_terms']} relF(F32 vs F64) = {err:.3e}, "
+          f"|mu32 - mu64| = {abs(out['mu'] - ref64['mu']):.2e}")
+    assert out["n_terms"] >= 7000
+    assert err < 1e-6
