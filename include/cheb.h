@@ -142,6 +142,19 @@ int cheb_plan_create(const cheb_bsr *P_out, int32_t precision, int32_t tile, che
 int cheb_plan_bind(cheb_plan *plan, void *plan_ws, size_t plan_ws_bytes, void *stream);
 int cheb_plan_info(const cheb_plan *plan, int64_t *n_panels, int32_t *panel_width,
                    int32_t *max_union);
+
+/* Operator pair lists (optional, for the per-step kernel).  For the operator
+ * pattern L (the M~ of the recursion), cheb_plan_attach_operator (host-
+ * returning) precomputes for every panel its union rows two at a time and, per
+ * pair, the merged list of L's blocks whose column lies in the panel's union;
+ * *op_ws_bytes receives the device memory the lists need.  After
+ * cheb_plan_bind_operator copies them into caller memory op_ws (256-byte
+ * aligned, kept valid until cheb_plan_destroy), every per-step product whose
+ * operator has exactly these row_ptr/col_idx pointers multiplies two rows per
+ * pass from the lists instead of ranking the operator's rows each step; other
+ * operators use the general path.  Results are the same up to summation order. */
+int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, size_t *op_ws_bytes, void *stream);
+int cheb_plan_bind_operator(cheb_plan *plan, void *op_ws, size_t op_ws_bytes, void *stream);
 int cheb_plan_destroy(cheb_plan *plan);
 
 /* ---------------------------------------------------------------------------

@@ -26,7 +26,7 @@ FERMI, ERFC, POWER, INTERVAL, PENALTY = 0, 1, 2, 3, 4
 # Every symbol declared in include/cheb.h.
 EXPORTS = [
     "cheb_last_error", "cheb_launch_count", "cheb_pattern_build", "cheb_tile_count", "cheb_tile_info", "cheb_plan_create", "cheb_plan_bind", "cheb_plan_info",
-    "cheb_plan_destroy", "cheb_scale", "cheb_bounds_workspace_size", "cheb_bounds",
+    "cheb_plan_destroy", "cheb_plan_attach_operator", "cheb_plan_bind_operator", "cheb_scale", "cheb_bounds_workspace_size", "cheb_bounds",
     "cheb_coeffs_workspace_size", "cheb_coeffs", "cheb_expand_workspace_size", "cheb_expand",
     "cheb_expand_stepwise_workspace_size", "cheb_expand_stepwise", "cheb_plan_create_batched",
     "cheb_plan_resident_info", "cheb_expand_batched", "cheb_lincomb", "cheb_mlp_param_count",
@@ -77,6 +77,8 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
         "cheb_plan_bind": ([p, p, sz, p], i32),
         "cheb_plan_info": ([p, P(i64), P(i32), P(i32)], i32),
         "cheb_plan_destroy": ([p], i32),
+        "cheb_plan_attach_operator": ([p, P(CBsr), P(sz), p], i32),
+        "cheb_plan_bind_operator": ([p, p, sz, p], i32),
         "cheb_scale": ([P(CBsr), dbl, dbl, p, p], i32),
         "cheb_bounds_workspace_size": ([i64, i32, P(sz)], i32),
         "cheb_bounds": ([P(CBsr), i32, p, dbl, P(dbl), P(dbl), P(dbl), p, sz, p], i32),
@@ -216,6 +218,18 @@ class Plan:
         self.handle = h
         self._ws = _ws(nbytes.value, P_out.row_ptr.device)
         _check(lib.cheb_plan_bind(h, ctypes.c_void_p(_aligned(self._ws)), nbytes.value, s))
+
+    def attach_operator(self, L: Bsr, stream=None) -> "Plan":
+        """cheb_plan_attach_operator + cheb_plan_bind_operator for operator pattern L."""
+        lib = load()
+        nbytes = ctypes.c_size_t(0)
+        s = _stream(stream)
+        cb = L.c()
+        _check(lib.cheb_plan_attach_operator(self.handle, ctypes.byref(cb), ctypes.byref(nbytes), s))
+        self._op_ws = _ws(nbytes.value, L.row_ptr.device)
+        self._op_pattern = (L.row_ptr, L.col_idx)  # the lists refer to these pointers
+        _check(lib.cheb_plan_bind_operator(self.handle, ctypes.c_void_p(_aligned(self._op_ws)), nbytes.value, s))
+        return self
 
     def info(self) -> tuple[int, int, int]:
         a, b, c = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()

@@ -52,6 +52,9 @@ struct StepArgs {
     double *part;  // per-block partials
     int32_t *counter;
     int32_t round_bf16;  // store T_{k+1} rounded to bfloat16 (CHEB_BF16 mode)
+    // operator pair lists of the plan (NULL: rank the operator's rows each step)
+    const int32_t *pair_ptr, *pair_rows, *ent_ptr, *ent_a;
+    const uint16_t *ent_s;
 };
 
 // x rounded to the nearest bfloat16 (ties to even), returned as float
@@ -132,6 +135,79 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
     }
     __syncthreads();
 
+    // 3p. with the plan's operator pair lists: two union rows per warp pass; each
+    // K-group walks the pair's merged in-union operator blocks, loads the panel
+    // block of T_k once and multiplies it into both rows' sums.
+    if (a.pair_ptr) {
+        const int q = lane % P, kg = lane / P;
+        const int t0 = a.pair_ptr[blockIdx.x], t1 = a.pair_ptr[blockIdx.x + 1];
+        for (int t = t0 + warp; t < t1; t += NW) {
+            const int s1 = a.pair_rows[2 * t], s2 = a.pair_rows[2 * t + 1];
+            const int e0 = a.ent_ptr[t], e1 = a.ent_ptr[t + 1];
+            T acc1[16], acc2[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                acc1[i] = T(0);
+                acc2[i] = T(0);
+            }
+            int e = e0 + kg;
+            int2 an = e < e1 ? reinterpret_cast<const int2 *>(a.ent_a)[e] : make_int2(-1, -1);
+            int sn = e < e1 ? (int)a.ent_s[e] : 0;
+            for (; e < e1; e += KG) {
+                const int2 aa = an;
+                const int sl = sn;
+                if (e + KG < e1) {
+                    an = reinterpret_cast<const int2 *>(a.ent_a)[e + KG];
+                    sn = (int)a.ent_s[e + KG];
+                }
+                T h1[16], h2[16];
+                if (aa.x >= 0) load16<T>(h1, a.Lv + (int64_t)aa.x * BB);
+                if (aa.y >= 0) load16<T>(h2, a.Lv + (int64_t)aa.y * BB);
+                const T *xs = X + sl * (BB * P) + 4 * q;
+                const int sw = sl & 1;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    T x[4];
+                    lds4<T>(x, xs + (m ^ sw) * 4 * P);
+                    if (aa.x >= 0) {
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) acc1[4 * r + c] = fma(h1[4 * r + m], x[c], acc1[4 * r + c]);
+                    }
+                    if (aa.y >= 0) {
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) acc2[4 * r + c] = fma(h2[4 * r + m], x[c], acc2[4 * r + c]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = P; o < 32; o <<= 1)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    acc1[i] += __shfl_xor_sync(0xffffffffu, acc1[i], o);
+                    acc2[i] += __shfl_xor_sync(0xffffffffu, acc2[i], o);
+                }
+            if (q < ncols && kg * EPL < 16) {
+                const int ea = pos[s1 * P + q];
+                if (ea >= 0) {
+                    const int64_t slot = (int64_t)a.tperm[a.rp[j0 + q] + ea] * BB;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (i / EPL == kg) a.C[slot + i] = acc1[i];
+                }
+                const int eb = s2 >= 0 ? pos[s2 * P + q] : -1;
+                if (eb >= 0) {
+                    const int64_t slot = (int64_t)a.tperm[a.rp[j0 + q] + eb] * BB;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (i / EPL == kg) a.C[slot + i] = acc2[i];
+                }
+            }
+        }
+    } else {
     // 3. union rows: masked block products M~_I. X for the panel's columns.
     // The row's blocks are ranked 32 at a time (one block per lane); those
     // whose column K is in the union go to the warp's staging ring.  Every 32
@@ -269,6 +345,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
             na1 = ma1;
         }
     }
+    }  // generic row phase
     __syncthreads();
 
     // 4. epilogue over the panel's output blocks, one block row (4 elements) per
@@ -422,6 +499,13 @@ StepArgs<T> base_args(const cheb_plan *plan, const cheb_bsr *L, const T *Lv) {
     a.Lrp = L->row_ptr;
     a.Lci = L->col_idx;
     a.Lv = Lv;
+    if (plan->op_bound && plan->op_rp == L->row_ptr && plan->op_ci == L->col_idx) {
+        a.pair_ptr = plan->d_pair_ptr;
+        a.pair_rows = plan->d_pair_rows;
+        a.ent_ptr = plan->d_ent_ptr;
+        a.ent_a = plan->d_ent_a;
+        a.ent_s = plan->d_ent_s;
+    }
     return a;
 }
 

@@ -275,3 +275,97 @@ extern "C" int cheb_plan_destroy(cheb_plan *plan) {
     delete plan;
     return CHEB_OK;
 }
+
+extern "C" int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, size_t *op_ws_bytes, void *stream) {
+    if (!plan || !L || !op_ws_bytes || !L->row_ptr || !L->col_idx || L->nbr != plan->nbr)
+        return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: bad arguments");
+    if (plan->ucap > 65535) return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: union too large");
+    const int64_t nbr = plan->nbr, nnzL = L->nnzb;
+    if (nnzL >= (int64_t)INT32_MAX) return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: operator too large");
+    std::vector<int64_t> rp(nbr + 1), lrp(nbr + 1);
+    std::vector<int32_t> ci(plan->nnzb), lci(nnzL);
+    cudaStream_t s = as_stream(stream);
+    CHEB_CUDA(cudaMemcpyAsync(rp.data(), plan->rp, (nbr + 1) * 8, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaMemcpyAsync(ci.data(), plan->ci, plan->nnzb * 4, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaMemcpyAsync(lrp.data(), L->row_ptr, (nbr + 1) * 8, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaMemcpyAsync(lci.data(), L->col_idx, nnzL * 4, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaStreamSynchronize(s));
+    if (lrp[0] != 0 || lrp[nbr] != nnzL) return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: bad row_ptr");
+    std::vector<int32_t> slot_of(nbr, -1), stamp(nbr, -1), uni;
+    std::vector<int32_t> pair_ptr{0}, pair_rows, ent_ptr{0}, ent_a;
+    std::vector<uint16_t> ent_s;
+    for (int64_t p = 0; p < plan->n_panels; ++p) {
+        const int32_t j0 = plan->h_panels[2 * p], nc = plan->h_panels[2 * p + 1];
+        uni.clear();
+        for (int32_t q = 0; q < nc; ++q)
+            for (int64_t e = rp[j0 + q]; e < rp[j0 + q + 1]; ++e)
+                if (stamp[ci[e]] != (int32_t)p) {
+                    stamp[ci[e]] = (int32_t)p;
+                    uni.push_back(ci[e]);
+                }
+        std::sort(uni.begin(), uni.end());
+        for (size_t u = 0; u < uni.size(); ++u) slot_of[uni[u]] = (int32_t)u;
+        for (size_t u = 0; u < uni.size(); u += 2) {
+            const int32_t I1 = uni[u], I2 = u + 1 < uni.size() ? uni[u + 1] : -1;
+            pair_rows.push_back((int32_t)u);
+            pair_rows.push_back(I2 >= 0 ? (int32_t)(u + 1) : -1);
+            int64_t a = lrp[I1], ae = lrp[I1 + 1];
+            int64_t b = I2 >= 0 ? lrp[I2] : 0, be = I2 >= 0 ? lrp[I2 + 1] : 0;
+            while (a < ae || b < be) {
+                const int32_t Ka = a < ae ? lci[a] : INT32_MAX, Kb = b < be ? lci[b] : INT32_MAX;
+                const int32_t K = std::min(Ka, Kb);
+                const int32_t ia = Ka == K ? (int32_t)a++ : -1;
+                const int32_t ib = Kb == K ? (int32_t)b++ : -1;
+                if (K < 0 || K >= nbr) return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: column out of range");
+                const int32_t sl = stamp[K] == (int32_t)p ? slot_of[K] : -1;
+                if (sl < 0) continue;  // K outside the union: T_k has no block in the panel's columns
+                ent_a.push_back(ia);
+                ent_a.push_back(ib);
+                ent_s.push_back((uint16_t)sl);
+            }
+            ent_ptr.push_back((int32_t)ent_s.size());
+            if (ent_s.size() >= (size_t)INT32_MAX) return fail(CHEB_ERR_NOSPACE, "cheb_plan_attach_operator: too many entries");
+        }
+        pair_ptr.push_back((int32_t)(pair_rows.size() / 2));
+    }
+    plan->op_rp = L->row_ptr;
+    plan->op_ci = L->col_idx;
+    plan->n_pairs = (int64_t)pair_rows.size() / 2;
+    plan->n_entries = (int64_t)ent_s.size();
+    plan->h_pair_ptr.swap(pair_ptr);
+    plan->h_pair_rows.swap(pair_rows);
+    plan->h_ent_ptr.swap(ent_ptr);
+    plan->h_ent_a.swap(ent_a);
+    plan->h_ent_s.swap(ent_s);
+    plan->op_ws_bytes = align_up(plan->h_pair_ptr.size() * 4) + align_up(plan->h_pair_rows.size() * 4) +
+                        align_up(plan->h_ent_ptr.size() * 4) + align_up(plan->h_ent_a.size() * 4) +
+                        align_up(plan->h_ent_s.size() * 2);
+    plan->op_bound = false;
+    *op_ws_bytes = plan->op_ws_bytes;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_bind_operator(cheb_plan *plan, void *ws, size_t ws_bytes, void *stream) {
+    if (!plan || plan->op_ws_bytes == 0) return fail(CHEB_ERR_INVALID, "cheb_plan_bind_operator: nothing attached");
+    if (!ws || ws_bytes < plan->op_ws_bytes || ((uintptr_t)ws) % 256)
+        return fail(CHEB_ERR_NOSPACE, "cheb_plan_bind_operator: workspace %zu < %zu or misaligned", ws_bytes,
+                    plan->op_ws_bytes);
+    Carve cv(ws, ws_bytes);
+    plan->d_pair_ptr = cv.take<int32_t>(plan->h_pair_ptr.size());
+    plan->d_pair_rows = cv.take<int32_t>(plan->h_pair_rows.size());
+    plan->d_ent_ptr = cv.take<int32_t>(plan->h_ent_ptr.size());
+    plan->d_ent_a = cv.take<int32_t>(plan->h_ent_a.size());
+    plan->d_ent_s = cv.take<uint16_t>(plan->h_ent_s.size());
+    cudaStream_t s = as_stream(stream);
+    CHEB_CUDA(cudaMemcpyAsync(plan->d_pair_ptr, plan->h_pair_ptr.data(), plan->h_pair_ptr.size() * 4, cudaMemcpyHostToDevice, s));
+    CHEB_CUDA(cudaMemcpyAsync(plan->d_pair_rows, plan->h_pair_rows.data(), plan->h_pair_rows.size() * 4, cudaMemcpyHostToDevice, s));
+    CHEB_CUDA(cudaMemcpyAsync(plan->d_ent_ptr, plan->h_ent_ptr.data(), plan->h_ent_ptr.size() * 4, cudaMemcpyHostToDevice, s));
+    CHEB_CUDA(cudaMemcpyAsync(plan->d_ent_a, plan->h_ent_a.data(), plan->h_ent_a.size() * 4, cudaMemcpyHostToDevice, s));
+    CHEB_CUDA(cudaMemcpyAsync(plan->d_ent_s, plan->h_ent_s.data(), plan->h_ent_s.size() * 2, cudaMemcpyHostToDevice, s));
+    CHEB_CUDA(cudaStreamSynchronize(s));
+    // the device copies are the only ones needed from here on
+    std::vector<int32_t>().swap(plan->h_ent_a);
+    std::vector<uint16_t>().swap(plan->h_ent_s);
+    plan->op_bound = true;
+    return CHEB_OK;
+}

@@ -42,6 +42,22 @@ struct cheb_plan {
     int32_t *d_rpanel_sys = nullptr;
     int32_t *d_sys_rpanel = nullptr;
     size_t ws_bytes = 0;
+    // Operator pair lists (cheb_plan_attach_operator): for every step panel, its
+    // union rows taken two at a time, and for each pair the merged list of the
+    // operator's in-union blocks: (block of row 1 or -1, block of row 2 or -1,
+    // union slot of K).  Valid for the operator pattern (op_rp, op_ci) only.
+    const int64_t *op_rp = nullptr;
+    const int32_t *op_ci = nullptr;
+    int64_t n_pairs = 0, n_entries = 0;
+    std::vector<int32_t> h_pair_ptr;   // [n_panels + 1]
+    std::vector<int32_t> h_pair_rows;  // [2 * n_pairs] union slots (second -1 if alone)
+    std::vector<int32_t> h_ent_ptr;    // [n_pairs + 1]
+    std::vector<int32_t> h_ent_a;      // [2 * n_entries]
+    std::vector<uint16_t> h_ent_s;     // [n_entries]
+    size_t op_ws_bytes = 0;
+    bool op_bound = false;
+    int32_t *d_pair_ptr = nullptr, *d_pair_rows = nullptr, *d_ent_ptr = nullptr, *d_ent_a = nullptr;
+    uint16_t *d_ent_s = nullptr;
 };
 
 namespace cheb {

@@ -137,11 +137,14 @@ def postprocess(pb: Problem, A: torch.Tensor, p: torch.Tensor) -> torch.Tensor:
 def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FERMI, n_max: int = 16384,
         lanczos_k: int = 40, tol_N: float | None = None, bounds_S=None, n_S=None, bounds_H=None, n_H=None,
         max_iter: int = 100, n_mu: int = 1, mu_stencil: float = 0.05, tol_S: float | None = None,
-        stepwise: bool = True, isqrt: str = "f64", timings: dict | None = None) -> dict:
+        stepwise: bool = True, isqrt: str = "f64", pair_lists: bool = False, timings: dict | None = None) -> dict:
     """Density matrix F with Tr(F S) = N_e (see the module docstring for the steps).
 
     isqrt: "f64" expands S^-1/2 in FP64; "f32ns" expands it in the problem's
     reduced precision and applies one FP64 Newton-Schulz correction.
+    pair_lists: precompute the H~' pair lists for the per-step kernel
+    (cheb_plan_attach_operator); measured slower on GB300 (5.6 vs 4.9 ms per
+    FP32 step at 40k rows), so off by default.
     """
     tm = {} if timings is None else timings
     t0 = time.perf_counter()
@@ -159,6 +162,8 @@ def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FE
     else:
         e0, e1 = bounds_H
     Hpt = Hp.with_vals(L.scale(Hp, e0, e1))
+    if stepwise and pair_lists:
+        pb.planX.attach_operator(Hpt)
     G = trace_functional(pb, A)
     mid = 0.5 * (e0 + e1)
     if n_H is None:

@@ -485,3 +485,30 @@ def test_mixed_precision_error_at_the_bench_degree():
           f"|mu32 - mu64| = {abs(out['mu'] - ref64['mu']):.2e}")
     assert out["n_terms"] >= 7000
     assert err < 1e-6
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_operator_pair_lists_match_oracle(prec):
+    n, nf = 40, 2
+    for n_atoms, r_c, r_buf in ((33, 3.0, 1.5), (300, 6.0, 3.0)):
+        s, H, P_out, e0, e1, Ht, coeffs, G = _expand_case(n_atoms, r_c, r_buf, 51 + n_atoms, n, nf)
+        ex = ref.chebyshev_expand(Ht, P_out, coeffs, G=G)
+        dP = dbsr(P_out.row_ptr, P_out.col_idx)
+        dHt = dbsr(Ht.row_ptr, Ht.col_idx, Ht.vals)
+        plan = cg.Plan(dP, prec).attach_operator(dHt)
+        acc = [torch.zeros((P_out.nnzb, 4, 4), dtype=torch.float64, device=DEV) for _ in range(nf)]
+        g = torch.zeros(n, dtype=torch.float64, device=DEV)
+        cg.expand(plan, dHt, n, torch.as_tensor(coeffs, device=DEV), acc, G=torch.as_tensor(G.vals, device=DEV),
+                  gmoments=g, precision=prec, stepwise=True)
+        tol = 1e-10 if prec == cg.F64 else 1e-5
+        for j in range(nf):
+            assert relF(acc[j].cpu().numpy(), ex.acc[j].vals) < tol
+        assert relF(g.cpu().numpy(), ex.g) < tol
+        # an operator with another pattern takes the general path on the same plan
+        dH = dbsr(H.row_ptr, H.col_idx, H.vals)
+        R = torch.as_tensor(np.random.default_rng(1).normal(size=(P_out.nnzb, 4, 4)), device=DEV)
+        if prec == cg.F64:
+            C = torch.empty_like(R)
+            cg.masked_product(plan, cg.Bsr(dH.row_ptr.clone(), dH.col_idx.clone(), dH.vals), R, C)
+            want = ref.masked_product(H, P_out.with_vals(R.cpu().numpy()), P_out.row_ptr, P_out.col_idx)
+            assert relF(C.cpu().numpy(), want) < 1e-13
