@@ -325,6 +325,38 @@ int cheb_mu_search(const double *gmoments, int32_t n_terms, double emin, double 
                    const double *bracket, void *result, void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * mu search without a workspace.  The paper has no counterpart: this is a
+ * library convenience.  It computes exactly what cheb_mu_search computes (same
+ * kernels, same arguments and result layout) for callers that cannot hand the
+ * library device memory -- e.g. a host loop that must not call cudaMalloc or
+ * cudaFree between steps (those calls can synchronise the whole device and
+ * stall the work of other streams), or a C caller with no device allocator at
+ * hand.  The call itself allocates nothing.
+ *
+ * Scratch: a fixed array of CHEB_MU_SEARCH_NOALLOC_MAX_TERMS doubles (128 KiB)
+ * in the library's own static device memory, one per device.  n_terms above
+ * that limit fails with CHEB_ERR_INVALID before anything is launched; use
+ * cheb_mu_search with a workspace for longer expansions.  Nothing in the
+ * scratch needs to start at zero: every one of the n_terms weights is written
+ * before it is read.
+ *
+ * Device: the current device of the calling thread; stream must belong to it.
+ * The first call on a device looks up the scratch's address there (a one-time
+ * set-up per device, guarded by a host mutex); make that first call before any
+ * stream capture.
+ *
+ * Overlap: all calls on one device share its scratch, so two calls whose work
+ * can overlap (different streams without an ordering between them, or
+ * different host threads) race and may return wrong results.  Calls issued to
+ * one stream, or otherwise ordered, are safe.  The result buffer is the
+ * caller's (device, 48 bytes, as in cheb_mu_search).  Asynchronous.
+ */
+#define CHEB_MU_SEARCH_NOALLOC_MAX_TERMS 16384
+int cheb_mu_search_noalloc(const double *gmoments, int32_t n_terms, double emin, double emax,
+                           int32_t kind, double kT, double N_e, double tol_N, int32_t max_iter,
+                           const double *bracket, void *result, void *stream);
+
+/* ---------------------------------------------------------------------------
  * One FP64 in-pattern Newton-Schulz step for S^-1 (not in the paper; repairs
  * the precision of a reduced-precision expansion):
  *   X1 = 2 X0 - P_out(X0 P_out(S X0)).

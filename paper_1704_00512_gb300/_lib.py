@@ -32,7 +32,7 @@ EXPORTS = [
     "cheb_plan_resident_info", "cheb_expand_batched", "cheb_lincomb", "cheb_mlp_param_count",
     "cheb_mlp_forward", "cheb_mlp_loss", "cheb_mlp_backward", "cheb_mlp_adam", "cheb_mlp_features",
     "cheb_masked_product", "cheb_transpose", "cheb_restrict", "cheb_trace_workspace_size", "cheb_trace",
-    "cheb_penalty_trace", "cheb_mu_search", "cheb_newton_schulz", "cheb_newton_schulz_isqrt",
+    "cheb_penalty_trace", "cheb_mu_search", "cheb_mu_search_noalloc", "cheb_newton_schulz", "cheb_newton_schulz_isqrt",
 ]
 
 
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
         "cheb_trace": ([P(CBsr), P(CBsr), p, p, sz, p], i32),
         "cheb_penalty_trace": ([p, i32, dbl, p, p, sz, p], i32),
         "cheb_mu_search": ([p, i32, dbl, dbl, i32, dbl, dbl, dbl, i32, p, p, p, sz, p], i32),
+        "cheb_mu_search_noalloc": ([p, i32, dbl, dbl, i32, dbl, dbl, dbl, i32, p, p, p], i32),
         "cheb_newton_schulz": ([p, P(CBsr), p, p, p, p], i32),
         "cheb_newton_schulz_isqrt": ([p, P(CBsr), p, p, p, p, p], i32),
     }
@@ -418,6 +419,24 @@ def mu_search(gmoments: torch.Tensor, n_terms: int, emin: float, emax: float, ki
     br = None if bracket is None else (ctypes.c_double * 2)(*bracket)
     _check(load().cheb_mu_search(_ptr(gmoments), n_terms, emin, emax, kind, kT, N_e, tol_N, max_iter, br,
                                  _ptr(res), ctypes.c_void_p(_aligned(ws)), 8 * n_terms, _stream(stream)))
+    return res
+
+
+MU_SEARCH_NOALLOC_MAX_TERMS = 16384  # CHEB_MU_SEARCH_NOALLOC_MAX_TERMS
+
+
+def mu_search_noalloc(gmoments: torch.Tensor, n_terms: int, emin: float, emax: float, kind: int, kT: float,
+                      N_e: float, tol_N: float, max_iter: int = 100, bracket: tuple[float, float] | None = None,
+                      result: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """cheb_mu_search_noalloc: the library's static scratch instead of a workspace.
+
+    Calls on one device share that scratch: do not overlap two of them (see
+    include/cheb.h).  result: optional 48-byte device uint8 tensor to reuse.
+    """
+    res = torch.zeros(48, dtype=torch.uint8, device=gmoments.device) if result is None else result
+    br = None if bracket is None else (ctypes.c_double * 2)(*bracket)
+    _check(load().cheb_mu_search_noalloc(_ptr(gmoments), n_terms, emin, emax, kind, kT, N_e, tol_N, max_iter, br,
+                                         _ptr(res), _stream(stream)))
     return res
 
 

@@ -2,6 +2,7 @@
 // (Eq. 5) and the mu bisection on the trace functional (Sec. "Fermi Operator
 // Expansion"), all in FP64.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -342,6 +343,60 @@ extern "C" int cheb_mu_search(const double *gmoments, int32_t n_terms, double em
     if (!ws || ws_bytes < (size_t)n_terms * 8) return fail(CHEB_ERR_NOSPACE, "cheb_mu_search: workspace");
     cudaStream_t s = as_stream(stream);
     double *w = static_cast<double *>(ws);
+    k_count_weights<<<(n_terms + 127) / 128, 128, 0, s>>>(gmoments, n_terms, w);
+    CHEB_TRY(check_launch("k_count_weights"));
+    const double lo = bracket ? bracket[0] : emin, hi = bracket ? bracket[1] : emax;
+    k_bisect<256><<<1, 256, 0, s>>>(w, n_terms, emin, emax, kind, kT, N_e, tol_N, max_iter, lo, hi,
+                                     static_cast<MuResult *>(result));
+    return check_launch("k_bisect");
+}
+
+// Workspace-free mu search (no counterpart in the paper).  The count weights
+// live in a static device array of the library; its address is looked up once
+// per device with that device current and cached under a host mutex.
+namespace cheb {
+
+static __device__ __align__(256) double g_mu_noalloc_w[CHEB_MU_SEARCH_NOALLOC_MAX_TERMS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static std::mutex g_mu_noalloc_mx;
+static double *g_mu_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+static int mu_noalloc_scratch(double **out) {
+    int dev = -1;
+    CHEB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return fail(CHEB_ERR_INVALID, "cheb_mu_search_noalloc: device %d beyond the %d supported", dev,
+                    NOALLOC_MAX_DEVICES);
+    std::lock_guard<std::mutex> lk(g_mu_noalloc_mx);
+    if (!g_mu_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_mu_noalloc_w);
+        if (e != cudaSuccess || !p)
+            return fail(CHEB_ERR_CUDA, "cheb_mu_search_noalloc: scratch address on device %d: %s", dev,
+                        cudaGetErrorString(e));
+        g_mu_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_mu_noalloc_ptr[dev];
+    return CHEB_OK;
+}
+
+}  // namespace cheb
+
+extern "C" int cheb_mu_search_noalloc(const double *gmoments, int32_t n_terms, double emin, double emax,
+                                      int32_t kind, double kT, double N_e, double tol_N, int32_t max_iter,
+                                      const double *bracket, void *result, void *stream) {
+    if (!gmoments || !result || n_terms < 2 || !(emax > emin) || max_iter < 1 || max_iter > 128 || !(kT > 0) ||
+        (kind != CHEB_FERMI && kind != CHEB_ERFC))
+        return fail(CHEB_ERR_INVALID, "cheb_mu_search_noalloc: bad arguments");
+    if (n_terms > CHEB_MU_SEARCH_NOALLOC_MAX_TERMS)
+        return fail(CHEB_ERR_INVALID,
+                    "cheb_mu_search_noalloc: n_terms %d exceeds the static scratch of %d terms; "
+                    "use cheb_mu_search with a workspace",
+                    n_terms, CHEB_MU_SEARCH_NOALLOC_MAX_TERMS);
+    double *w = nullptr;
+    CHEB_TRY(mu_noalloc_scratch(&w));
+    cudaStream_t s = as_stream(stream);
     k_count_weights<<<(n_terms + 127) / 128, 128, 0, s>>>(gmoments, n_terms, w);
     CHEB_TRY(check_launch("k_count_weights"));
     const double lo = bracket ? bracket[0] : emin, hi = bracket ? bracket[1] : emax;
