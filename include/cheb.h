@@ -143,16 +143,21 @@ int cheb_plan_bind(cheb_plan *plan, void *plan_ws, size_t plan_ws_bytes, void *s
 int cheb_plan_info(const cheb_plan *plan, int64_t *n_panels, int32_t *panel_width,
                    int32_t *max_union);
 
-/* Operator pair lists (optional, for the per-step kernel).  For the operator
- * pattern L (the M~ of the recursion), cheb_plan_attach_operator (host-
- * returning) precomputes for every panel its union rows two at a time and, per
- * pair, the merged list of L's blocks whose column lies in the panel's union;
- * *op_ws_bytes receives the device memory the lists need.  After
- * cheb_plan_bind_operator copies them into caller memory op_ws (256-byte
- * aligned, kept valid until cheb_plan_destroy), every per-step product whose
- * operator has exactly these row_ptr/col_idx pointers multiplies two rows per
- * pass from the lists instead of ranking the operator's rows each step; other
- * operators use the general path.  Results are the same up to summation order. */
+/* Operator row lists (optional, for the per-step kernel; the gather plan of the
+ * masked product restricted to each panel).  For the operator pattern L (the
+ * M~ of the recursion), cheb_plan_attach_operator (host-returning) precomputes
+ * for every panel and each row I of the union of its columns' row lists the
+ * blocks L_IK whose column K lies in that union, as 32-bit words (offset of
+ * the block within row I of L) << 16 | (rank of K in the union); rows of L
+ * must hold at most 65536 blocks.  *op_ws_bytes receives the device memory
+ * the lists need (about 4 bytes per entry, plus 4 per (panel, union row) and
+ * 8 per panel).  After cheb_plan_bind_operator copies them into caller memory
+ * op_ws (256-byte aligned, kept valid until cheb_plan_destroy or the next
+ * attach), every per-step product whose operator has exactly these
+ * row_ptr/col_idx pointers reads its entries from the lists instead of
+ * ranking the operator's rows at every step; other operators use the ranking
+ * path.  Both paths multiply the same blocks in the same order, so results
+ * are bit-identical.  Attaching again replaces the lists. */
 int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, size_t *op_ws_bytes, void *stream);
 int cheb_plan_bind_operator(cheb_plan *plan, void *op_ws, size_t op_ws_bytes, void *stream);
 int cheb_plan_destroy(cheb_plan *plan);

@@ -221,14 +221,14 @@ class Plan:
         _check(lib.cheb_plan_bind(h, ctypes.c_void_p(_aligned(self._ws)), nbytes.value, s))
 
     def attach_operator(self, L: Bsr, stream=None) -> "Plan":
-        """cheb_plan_attach_operator + cheb_plan_bind_operator for operator pattern L."""
+        """cheb_plan_attach_operator + cheb_plan_bind_operator: row lists for operator pattern L."""
         lib = load()
         nbytes = ctypes.c_size_t(0)
         s = _stream(stream)
         cb = L.c()
         _check(lib.cheb_plan_attach_operator(self.handle, ctypes.byref(cb), ctypes.byref(nbytes), s))
         self._op_ws = _ws(nbytes.value, L.row_ptr.device)
-        self._op_pattern = (L.row_ptr, L.col_idx)  # the lists refer to these pointers
+        self._op_pattern = (L.row_ptr, L.col_idx)  # the lists are used for operators with these pointers
         _check(lib.cheb_plan_bind_operator(self.handle, ctypes.c_void_p(_aligned(self._op_ws)), nbytes.value, s))
         return self
 

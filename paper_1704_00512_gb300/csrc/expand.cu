@@ -52,9 +52,10 @@ struct StepArgs {
     double *part;  // per-block partials
     int32_t *counter;
     int32_t round_bf16;  // store T_{k+1} rounded to bfloat16 (CHEB_BF16 mode)
-    // operator pair lists of the plan (NULL: rank the operator's rows each step)
-    const int32_t *pair_ptr, *pair_rows, *ent_ptr, *ent_a;
-    const uint16_t *ent_s;
+    // operator row lists of the plan (NULL: rank the operator's rows each step)
+    const int64_t *lrow_base;
+    const int32_t *lrow_ptr;
+    const uint32_t *lent;
 };
 
 // x rounded to the nearest bfloat16 (ties to even), returned as float
@@ -67,12 +68,13 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
     __shared__ int wsum[32];
     constexpr int NT = NW * 32;
     constexpr int KG = 32 / P;                  // K-groups per warp
-    constexpr int NU = 32 / KG;                 // staged entries per K-group per 32-chunk
+    constexpr int BT = step_batch(P);          // operator blocks per staged batch
+    constexpr int NU = BT / KG;                 // staged entries per K-group per batch
     constexpr int EPL = KG >= 16 ? 1 : 16 / KG;  // raw-store elements per lane
     const StepLayout lay = step_layout(a.nw, a.ucap, P, sizeof(T), NW);
     uint2 *bits = reinterpret_cast<uint2 *>(smem + lay.off_bits);
     int32_t *ulist = reinterpret_cast<int32_t *>(smem + lay.off_ulist);
-    int16_t *pos = reinterpret_cast<int16_t *>(smem + lay.off_pos);
+    int32_t *oslot = reinterpret_cast<int32_t *>(smem + lay.off_pos);
     int2 *wlist = reinterpret_cast<int2 *>(smem + lay.off_wl);
     int *bslot = reinterpret_cast<int *>(smem + lay.off_bslot);
     T *hbuf = reinterpret_cast<T *>(smem + lay.off_hbuf);
@@ -114,7 +116,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
         uint4 *x4 = reinterpret_cast<uint4 *>(X);
         const int64_t n4 = (int64_t)nu * BB * P * sizeof(T) / 16;
         for (int64_t i = tid; i < n4; i += NT) x4[i] = make_uint4(0u, 0u, 0u, 0u);
-        for (int64_t i = tid; i < (int64_t)nu * P; i += NT) pos[i] = -1;
+        for (int64_t i = tid; i < (int64_t)nu * P; i += NT) oslot[i] = -1;
     }
     __syncthreads();
     for (int q = 0; q < ncols; ++q) {
@@ -123,112 +125,43 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
             const int K = a.ci[p];
             const int s = rank_of(bits, K);
             T v[16];
-            load16<T>(v, a.R + (int64_t)a.tperm[p] * BB);
-            T *xs = X + (int64_t)s * BB * P;
+            const int32_t o = a.tperm[p];
+            load16<T>(v, a.R + (int64_t)o * BB);
+            T *xs = X + (int64_t)s * BB * P + 4 * q;
             const int sw = s & 1;
 #pragma unroll
-            for (int m = 0; m < 4; ++m)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) xs[((m ^ sw) * 4 * P) + 4 * q + c] = v[4 * m + c];
-            pos[s * P + q] = (int16_t)(p - b);
+            for (int m = 0; m < 4; ++m) {
+                const T r4[4] = {v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]};
+                Vec4<T>::st(xs + (m ^ sw) * 4 * P, r4);
+            }
+            oslot[s * P + q] = o;
         }
     }
     __syncthreads();
 
-    // 3p. with the plan's operator pair lists: two union rows per warp pass; each
-    // K-group walks the pair's merged in-union operator blocks, loads the panel
-    // block of T_k once and multiplies it into both rows' sums.
-    if (a.pair_ptr) {
-        const int q = lane % P, kg = lane / P;
-        const int t0 = a.pair_ptr[blockIdx.x], t1 = a.pair_ptr[blockIdx.x + 1];
-        for (int t = t0 + warp; t < t1; t += NW) {
-            const int s1 = a.pair_rows[2 * t], s2 = a.pair_rows[2 * t + 1];
-            const int e0 = a.ent_ptr[t], e1 = a.ent_ptr[t + 1];
-            T acc1[16], acc2[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                acc1[i] = T(0);
-                acc2[i] = T(0);
-            }
-            int e = e0 + kg;
-            int2 an = e < e1 ? reinterpret_cast<const int2 *>(a.ent_a)[e] : make_int2(-1, -1);
-            int sn = e < e1 ? (int)a.ent_s[e] : 0;
-            for (; e < e1; e += KG) {
-                const int2 aa = an;
-                const int sl = sn;
-                if (e + KG < e1) {
-                    an = reinterpret_cast<const int2 *>(a.ent_a)[e + KG];
-                    sn = (int)a.ent_s[e + KG];
-                }
-                T h1[16], h2[16];
-                if (aa.x >= 0) load16<T>(h1, a.Lv + (int64_t)aa.x * BB);
-                if (aa.y >= 0) load16<T>(h2, a.Lv + (int64_t)aa.y * BB);
-                const T *xs = X + sl * (BB * P) + 4 * q;
-                const int sw = sl & 1;
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    T x[4];
-                    lds4<T>(x, xs + (m ^ sw) * 4 * P);
-                    if (aa.x >= 0) {
-#pragma unroll
-                        for (int r = 0; r < 4; ++r)
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) acc1[4 * r + c] = fma(h1[4 * r + m], x[c], acc1[4 * r + c]);
-                    }
-                    if (aa.y >= 0) {
-#pragma unroll
-                        for (int r = 0; r < 4; ++r)
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) acc2[4 * r + c] = fma(h2[4 * r + m], x[c], acc2[4 * r + c]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int o = P; o < 32; o <<= 1)
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    acc1[i] += __shfl_xor_sync(0xffffffffu, acc1[i], o);
-                    acc2[i] += __shfl_xor_sync(0xffffffffu, acc2[i], o);
-                }
-            if (q < ncols && kg * EPL < 16) {
-                const int ea = pos[s1 * P + q];
-                if (ea >= 0) {
-                    const int64_t slot = (int64_t)a.tperm[a.rp[j0 + q] + ea] * BB;
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (i / EPL == kg) a.C[slot + i] = acc1[i];
-                }
-                const int eb = s2 >= 0 ? pos[s2 * P + q] : -1;
-                if (eb >= 0) {
-                    const int64_t slot = (int64_t)a.tperm[a.rp[j0 + q] + eb] * BB;
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (i / EPL == kg) a.C[slot + i] = acc2[i];
-                }
-            }
-        }
-    } else {
     // 3. union rows: masked block products M~_I. X for the panel's columns.
-    // The row's blocks are ranked 32 at a time (one block per lane); those
-    // whose column K is in the union go to the warp's staging ring.  Every 32
-    // staged entries form a batch whose operator blocks are copied to shared
-    // memory with asynchronous copies (cp.async); the batch before it is
-    // multiplied while they are in flight.  In a batch each K-group takes NU
-    // entries; a lane multiplies the 4x4 operator block by the panel block of
-    // its column q.
+    // Each warp takes union rows s = warp, warp + NW, ...; the in-union
+    // operator blocks of its rows form one stream of batches of up to BT.  A
+    // batch's operator blocks are copied to shared memory with asynchronous
+    // copies (cp.async) while the batch before it is multiplied; a row's last
+    // batch may be followed by the next row's first, so the next row's blocks
+    // are in flight while the current row is finished.  A batch never spans
+    // two rows.  In a batch each of the 32/P K-groups takes every (32/P)-th
+    // entry; a lane multiplies the 4x4 operator block by the panel block of
+    // its column q.  The batch's entries come either from the plan's operator
+    // row lists (precomputed per panel and union row) or, without lists, from
+    // ranking the operator row's column indices against the union bitmap.
     {
         const int q = lane % P, kg = lane / P;
-        const unsigned lt = (1u << lane) - 1u;
-        int2 *wl = wlist + warp * 64;
-        // two batches of 32 staged blocks, chunks XOR-swizzled like the panel blocks
-        unsigned char *hb = reinterpret_cast<unsigned char *>(hbuf + (size_t)warp * 2 * 32 * BB);
-        int *bs = bslot + warp * 64;                 // union slots of the staged blocks
-        auto issue = [&](int buf, int n) {
+        // two batches of BT staged blocks, chunks XOR-swizzled like the panel blocks
+        unsigned char *hb = reinterpret_cast<unsigned char *>(hbuf + (size_t)warp * 2 * BT * BB);
+        int *bs = bslot + warp * 64;  // union slots of the staged blocks
+        // batch entry of this lane: operator block index, union slot
+        auto issue = [&](int buf, int n, int64_t blk, int slot) {
             if (lane < n) {
-                const int2 e = wl[lane];
-                bs[buf * 32 + lane] = e.y;
-                const T *src = a.Lv + (int64_t)e.x * BB;
-                const int b = buf * 32 + lane;
+                bs[buf * BT + lane] = slot;
+                const T *src = a.Lv + blk * BB;
+                const int b = buf * BT + lane;
 #pragma unroll
                 for (int c = 0; c < (int)(BB * sizeof(T) / 16); ++c)
                     cp_async16(hb + rchunk<T>(b, c), src + c * (16 / sizeof(T)));
@@ -241,8 +174,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
                 const int e = u * KG + kg;
                 if (e >= n) continue;
                 T h[16];
-                r_ld<T>(h, hb, buf * 32 + e);
-                const int s2 = bs[buf * 32 + e];
+                r_ld<T>(h, hb, buf * BT + e);
+                const int s2 = bs[buf * BT + e];
                 const T *xs = X + s2 * (BB * P) + 4 * q;
                 const int sw = s2 & 1;
 #pragma unroll
@@ -256,96 +189,203 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
                 }
             }
         };
-        // Row bounds and the first 32 column indices are fetched one row ahead
-        // (the bounds two rows ahead) so their latency overlaps the current row.
-        int64_t ca0 = 0, ca1 = 0, na0 = 0, na1 = 0;
-        if (warp < nu) {
-            const int I0 = ulist[warp];
-            ca0 = a.Lrp[I0];
-            ca1 = a.Lrp[I0 + 1];
-        }
-        int Kc = (warp < nu && ca0 + lane < ca1) ? a.Lci[ca0 + lane] : -1;
-        if (warp + NW < nu) {
-            const int I1 = ulist[warp + NW];
-            na0 = a.Lrp[I1];
-            na1 = a.Lrp[I1 + 1];
-        }
-        for (int s = warp; s < nu; s += NW) {
-            const int Kn = (s + NW < nu && na0 + lane < na1) ? a.Lci[na0 + lane] : -1;
-            int64_t ma0 = 0, ma1 = 0;
-            if (s + 2 * NW < nu) {
-                const int I2 = ulist[s + 2 * NW];
-                ma0 = a.Lrp[I2];
-                ma1 = a.Lrp[I2 + 1];
-            }
-            const int64_t a0 = ca0, a1 = ca1;
-            T acc[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) acc[i] = T(0);
-            int pending = 0, inflight = -1, n_inflight = 0, nb = 0;
-            int64_t base = a0;
-            int Knext = Kc;
-            while (true) {
-                if (base < a1) {
-                    const int K = Knext;
-                    Knext = (base + 32 + lane < a1) ? a.Lci[base + 32 + lane] : -1;
-                    const int s2 = K >= 0 ? rank_of(bits, K) : -1;
-                    const unsigned vm = __ballot_sync(0xffffffffu, s2 >= 0);
-                    if (s2 >= 0) wl[pending + __popc(vm & lt)] = make_int2((int)(base + lane), s2);
-                    pending += __popc(vm);
-                    base += 32;
-                    __syncwarp();
-                }
-                const bool raw_done = base >= a1;
-                if (pending >= 32 || (raw_done && pending > 0)) {
-                    const int n = pending < 32 ? pending : 32;
-                    issue(nb, n);
-                    __syncwarp();
-                    const int rest = pending - n;
-                    const int2 keep = lane < rest ? wl[n + lane] : make_int2(0, 0);
-                    __syncwarp();
-                    if (lane < rest) wl[lane] = keep;
-                    pending = rest;
-                    if (inflight >= 0) {
-                        cp_async_wait<1>();
-                        __syncwarp();
-                        compute(acc, inflight, n_inflight);
-                    }
-                    inflight = nb;
-                    n_inflight = n;
-                    nb ^= 1;
-                    __syncwarp();
-                }
-                if (raw_done && pending == 0) break;
-            }
-            if (inflight >= 0) {
-                cp_async_wait<0>();
-                __syncwarp();
-                compute(acc, inflight, n_inflight);
-            }
-            __syncwarp();
+        auto finish_row = [&](T(&acc)[16], int s) {
 #pragma unroll
             for (int o = P; o < 32; o <<= 1)
 #pragma unroll
                 for (int i = 0; i < 16; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
             // raw product into the output slot; the epilogue below finishes it
             if (q < ncols && kg * EPL < 16) {
-                const int e = pos[s * P + q];
+                const int e = oslot[s * P + q];
                 if (e >= 0) {
-                    const int64_t slot = (int64_t)a.tperm[a.rp[j0 + q] + e] * BB;
+                    const int64_t slot = (int64_t)e * BB;
 #pragma unroll
                     for (int i = 0; i < 16; ++i)
                         if (i / EPL == kg) a.C[slot + i] = acc[i];
                 }
             }
-            ca0 = na0;
-            ca1 = na1;
-            Kc = Kn;
-            na0 = ma0;
-            na1 = ma1;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] = T(0);
+        };
+        // consumer: the batch in flight, its row slot and whether it ends the row
+        T acc[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[i] = T(0);
+        int inflight = -1, n_inflight = 0, row_inflight = 0, last_inflight = 0, nb = 0;
+        auto consume = [&](bool got) {
+            if (inflight < 0) return;
+            if (got)
+                cp_async_wait<1>();
+            else
+                cp_async_wait<0>();
+            __syncwarp();
+            compute(acc, inflight, n_inflight);
+            if (last_inflight) finish_row(acc, row_inflight);
+            __syncwarp();
+        };
+        auto advance = [&](int n, int prow, int plast) {
+            inflight = nb;
+            n_inflight = n;
+            row_inflight = prow;
+            last_inflight = plast;
+            nb ^= 1;
+        };
+        if (a.lrow_ptr) {
+            // Operator row lists: entries [rptr[s], rptr[s+1]) of union row s,
+            // each (offset of the block in the operator row << 16 | union slot).
+            // The entry words of a row's next batch are loaded one batch ahead;
+            // the following row's range, operator row start and first words one
+            // row ahead, and the range of the row after it two rows ahead.
+            const int32_t *rptr = a.lrow_ptr + a.lrow_base[blockIdx.x];
+            int ps = warp;
+            int64_t e = 0, e1 = 0, ab = 0, ne0 = 0, ne1 = 0, nab = 0, me0 = 0, me1 = 0, mab = 0;
+            if (ps < nu) {
+                e = rptr[ps];
+                e1 = rptr[ps + 1];
+                ab = a.Lrp[ulist[ps]];
+            }
+            uint32_t wcur = (ps < nu && lane < BT && e + lane < e1) ? a.lent[e + lane] : 0u;
+            if (ps + NW < nu) {
+                ne0 = rptr[ps + NW];
+                ne1 = rptr[ps + NW + 1];
+                nab = a.Lrp[ulist[ps + NW]];
+            }
+            uint32_t wnext = (ps + NW < nu && lane < BT && ne0 + lane < ne1) ? a.lent[ne0 + lane] : 0u;
+            if (ps + 2 * NW < nu) {
+                me0 = rptr[ps + 2 * NW];
+                me1 = rptr[ps + 2 * NW + 1];
+                mab = a.Lrp[ulist[ps + 2 * NW]];
+            }
+            while (true) {
+                const bool got = ps < nu;
+                int n = 0, prow = ps, plast = 0;
+                if (got) {
+                    // an empty row issues one empty batch, so that its zero product is stored
+                    n = (int)(e1 - e < BT ? e1 - e : BT);
+                    issue(nb, n, ab + (int64_t)(wcur >> 16), (int)(wcur & 0xffffu));
+                    e += n;
+                    if (e >= e1) {
+                        plast = 1;
+                        ps += NW;
+                        e = ne0;
+                        e1 = ne1;
+                        ab = nab;
+                        wcur = wnext;
+                        ne0 = me0;
+                        ne1 = me1;
+                        nab = mab;
+                        wnext = (ps + NW < nu && lane < BT && ne0 + lane < ne1) ? a.lent[ne0 + lane] : 0u;
+                        if (ps + 2 * NW < nu) {
+                            me0 = rptr[ps + 2 * NW];
+                            me1 = rptr[ps + 2 * NW + 1];
+                            mab = a.Lrp[ulist[ps + 2 * NW]];
+                        }
+                    } else {
+                        wcur = (lane < BT && e + lane < e1) ? a.lent[e + lane] : 0u;
+                    }
+                }
+                consume(got);
+                if (!got) break;
+                advance(n, prow, plast);
+            }
+        } else {
+            // Ranking: the row's column indices are ranked 32 at a time (one per
+            // lane) against the union bitmap; those in the union go to the
+            // warp's staging ring wl, from which batches of BT are issued.
+            const unsigned lt = (1u << lane) - 1u;
+            int2 *wl = wlist + warp * 64;
+            // producer: row slot ps being staged, its unranked range [base, a1)
+            // and its next 64 column indices (two chunks); the following row's
+            // bounds and first 64 indices, and the bounds of the row after it,
+            // are fetched ahead.
+            int ps = warp;
+            int64_t base = 0, a1 = 0, na0 = 0, na1 = 0, ma0 = 0, ma1 = 0;
+            if (ps < nu) {
+                const int I0 = ulist[ps];
+                base = a.Lrp[I0];
+                a1 = a.Lrp[I0 + 1];
+            }
+            int Kq1 = (ps < nu && base + lane < a1) ? a.Lci[base + lane] : -1;
+            int Kq2 = (ps < nu && base + 32 + lane < a1) ? a.Lci[base + 32 + lane] : -1;
+            if (ps + NW < nu) {
+                const int I1 = ulist[ps + NW];
+                na0 = a.Lrp[I1];
+                na1 = a.Lrp[I1 + 1];
+            }
+            int Kn1 = (ps + NW < nu && na0 + lane < na1) ? a.Lci[na0 + lane] : -1;
+            int Kn2 = (ps + NW < nu && na0 + 32 + lane < na1) ? a.Lci[na0 + 32 + lane] : -1;
+            if (ps + 2 * NW < nu) {
+                const int I2 = ulist[ps + 2 * NW];
+                ma0 = a.Lrp[I2];
+                ma1 = a.Lrp[I2 + 1];
+            }
+            int pending = 0, row_issued = 0;
+            while (true) {
+                int n = 0, prow = 0, plast = 0;
+                bool got = false;
+                while (ps < nu) {
+                    if (base < a1 && pending < BT) {
+                        const int K = Kq1;
+                        Kq1 = Kq2;
+                        Kq2 = (base + 64 + lane < a1) ? a.Lci[base + 64 + lane] : -1;
+                        const int s2 = K >= 0 ? rank_of(bits, K) : -1;
+                        const unsigned vm = __ballot_sync(0xffffffffu, s2 >= 0);
+                        if (s2 >= 0) wl[pending + __popc(vm & lt)] = make_int2((int)(base + lane), s2);
+                        pending += __popc(vm);
+                        base += 32;
+                        __syncwarp();
+                        continue;
+                    }
+                    // pending >= BT, or every raw entry of the row is ranked.  A
+                    // row with no operator block in the union issues one empty
+                    // batch, so that its (zero) product is still stored.
+                    n = pending < BT ? pending : BT;
+                    prow = ps;
+                    if (n > 0 || !row_issued) {
+                        const int2 w = lane < n ? wl[lane] : make_int2(0, 0);
+                        issue(nb, n, (int64_t)w.x, w.y);
+                        __syncwarp();
+                        const int rest = pending - n;
+                        const int2 keep = lane < rest ? wl[n + lane] : make_int2(0, 0);
+                        __syncwarp();
+                        if (lane < rest) wl[lane] = keep;
+                        pending = rest;
+                        __syncwarp();
+                        got = true;
+                        row_issued = 1;
+                    }
+                    if (base >= a1 && pending == 0) {  // row fully staged: advance
+                        // the row's last batch: the one just issued, or (when the
+                        // row's remaining raw entries were all outside the union)
+                        // the one in flight, which is always this row's latest
+                        if (got)
+                            plast = 1;
+                        else
+                            last_inflight = 1;
+                        row_issued = 0;
+                        ps += NW;
+                        base = na0;
+                        a1 = na1;
+                        Kq1 = Kn1;
+                        Kq2 = Kn2;
+                        na0 = ma0;
+                        na1 = ma1;
+                        Kn1 = (ps + NW < nu && na0 + lane < na1) ? a.Lci[na0 + lane] : -1;
+                        Kn2 = (ps + NW < nu && na0 + 32 + lane < na1) ? a.Lci[na0 + 32 + lane] : -1;
+                        if (ps + 2 * NW < nu) {
+                            const int I2 = ulist[ps + 2 * NW];
+                            ma0 = a.Lrp[I2];
+                            ma1 = a.Lrp[I2 + 1];
+                        }
+                    }
+                    if (got) break;
+                }
+                consume(got);
+                if (!got) break;
+                advance(n, prow, plast);
+            }
         }
     }
-    }  // generic row phase
     __syncthreads();
 
     // 4. epilogue over the panel's output blocks, one block row (4 elements) per
@@ -500,11 +540,9 @@ StepArgs<T> base_args(const cheb_plan *plan, const cheb_bsr *L, const T *Lv) {
     a.Lci = L->col_idx;
     a.Lv = Lv;
     if (plan->op_bound && plan->op_rp == L->row_ptr && plan->op_ci == L->col_idx) {
-        a.pair_ptr = plan->d_pair_ptr;
-        a.pair_rows = plan->d_pair_rows;
-        a.ent_ptr = plan->d_ent_ptr;
-        a.ent_a = plan->d_ent_a;
-        a.ent_s = plan->d_ent_s;
+        a.lrow_base = plan->d_lrow_base;
+        a.lrow_ptr = plan->d_lrow_ptr;
+        a.lent = plan->d_lent;
     }
     return a;
 }

@@ -9,6 +9,7 @@
 // the panel has fewer than P columns and the union of the panel's row lists
 // still fits the shared-memory budget.
 #include <algorithm>
+#include <thread>
 
 #include "common.cuh"
 #include "plan.cuh"
@@ -276,6 +277,45 @@ extern "C" int cheb_plan_destroy(cheb_plan *plan) {
     return CHEB_OK;
 }
 
+// Panels [p0, p1) of the operator row lists: with count_only, the number of
+// list entries of each panel; otherwise the row pointers and entries, written
+// at the panel offsets the counts gave.
+static void build_row_lists(const cheb_plan *plan, const std::vector<int64_t> &rp, const std::vector<int32_t> &ci,
+                            const std::vector<int64_t> &lrp, const std::vector<int32_t> &lci, int64_t p0, int64_t p1,
+                            bool count_only, std::vector<int64_t> &cnt, std::vector<int64_t> &nrow,
+                            const std::vector<int64_t> &ent_off, std::vector<int32_t> &lrow_ptr,
+                            std::vector<int64_t> &lrow_base, std::vector<uint32_t> &lent) {
+    std::vector<int32_t> stamp(plan->nbr, -1), slot_of(plan->nbr, -1), uni;
+    for (int64_t p = p0; p < p1; ++p) {
+        const int32_t j0 = plan->h_panels[2 * p], nc = plan->h_panels[2 * p + 1];
+        uni.clear();
+        for (int32_t q = 0; q < nc; ++q)
+            for (int64_t e = rp[j0 + q]; e < rp[j0 + q + 1]; ++e)
+                if (stamp[ci[e]] != (int32_t)p) {
+                    stamp[ci[e]] = (int32_t)p;
+                    uni.push_back(ci[e]);
+                }
+        std::sort(uni.begin(), uni.end());
+        for (size_t u = 0; u < uni.size(); ++u) slot_of[uni[u]] = (int32_t)u;
+        if (count_only) {
+            int64_t c = 0;
+            for (const int32_t I : uni)
+                for (int64_t a = lrp[I]; a < lrp[I + 1]; ++a) c += stamp[lci[a]] == (int32_t)p;
+            cnt[p] = c;
+            nrow[p] = (int64_t)uni.size() + 1;
+            continue;
+        }
+        int64_t w = ent_off[p], r = lrow_base[p];
+        for (const int32_t I : uni) {
+            lrow_ptr[r++] = (int32_t)w;
+            for (int64_t a = lrp[I]; a < lrp[I + 1]; ++a)
+                if (stamp[lci[a]] == (int32_t)p)
+                    lent[w++] = ((uint32_t)(a - lrp[I]) << 16) | (uint32_t)slot_of[lci[a]];
+        }
+        lrow_ptr[r] = (int32_t)w;
+    }
+}
+
 extern "C" int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, size_t *op_ws_bytes, void *stream) {
     if (!plan || !L || !op_ws_bytes || !L->row_ptr || !L->col_idx || L->nbr != plan->nbr)
         return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: bad arguments");
@@ -291,55 +331,52 @@ extern "C" int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, siz
     CHEB_CUDA(cudaMemcpyAsync(lci.data(), L->col_idx, nnzL * 4, cudaMemcpyDeviceToHost, s));
     CHEB_CUDA(cudaStreamSynchronize(s));
     if (lrp[0] != 0 || lrp[nbr] != nnzL) return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: bad row_ptr");
-    std::vector<int32_t> slot_of(nbr, -1), stamp(nbr, -1), uni;
-    std::vector<int32_t> pair_ptr{0}, pair_rows, ent_ptr{0}, ent_a;
-    std::vector<uint16_t> ent_s;
-    for (int64_t p = 0; p < plan->n_panels; ++p) {
-        const int32_t j0 = plan->h_panels[2 * p], nc = plan->h_panels[2 * p + 1];
-        uni.clear();
-        for (int32_t q = 0; q < nc; ++q)
-            for (int64_t e = rp[j0 + q]; e < rp[j0 + q + 1]; ++e)
-                if (stamp[ci[e]] != (int32_t)p) {
-                    stamp[ci[e]] = (int32_t)p;
-                    uni.push_back(ci[e]);
-                }
-        std::sort(uni.begin(), uni.end());
-        for (size_t u = 0; u < uni.size(); ++u) slot_of[uni[u]] = (int32_t)u;
-        for (size_t u = 0; u < uni.size(); u += 2) {
-            const int32_t I1 = uni[u], I2 = u + 1 < uni.size() ? uni[u + 1] : -1;
-            pair_rows.push_back((int32_t)u);
-            pair_rows.push_back(I2 >= 0 ? (int32_t)(u + 1) : -1);
-            int64_t a = lrp[I1], ae = lrp[I1 + 1];
-            int64_t b = I2 >= 0 ? lrp[I2] : 0, be = I2 >= 0 ? lrp[I2 + 1] : 0;
-            while (a < ae || b < be) {
-                const int32_t Ka = a < ae ? lci[a] : INT32_MAX, Kb = b < be ? lci[b] : INT32_MAX;
-                const int32_t K = std::min(Ka, Kb);
-                const int32_t ia = Ka == K ? (int32_t)a++ : -1;
-                const int32_t ib = Kb == K ? (int32_t)b++ : -1;
-                if (K < 0 || K >= nbr) return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: column out of range");
-                const int32_t sl = stamp[K] == (int32_t)p ? slot_of[K] : -1;
-                if (sl < 0) continue;  // K outside the union: T_k has no block in the panel's columns
-                ent_a.push_back(ia);
-                ent_a.push_back(ib);
-                ent_s.push_back((uint16_t)sl);
-            }
-            ent_ptr.push_back((int32_t)ent_s.size());
-            if (ent_s.size() >= (size_t)INT32_MAX) return fail(CHEB_ERR_NOSPACE, "cheb_plan_attach_operator: too many entries");
-        }
-        pair_ptr.push_back((int32_t)(pair_rows.size() / 2));
+    for (int64_t I = 0; I < nbr; ++I) {
+        if (lrp[I + 1] < lrp[I] || lrp[I + 1] - lrp[I] > 65536)
+            return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: row_ptr decreasing or row longer than 65536 blocks at row %lld",
+                        (long long)I);
+        for (int64_t a = lrp[I]; a < lrp[I + 1]; ++a)
+            if (lci[a] < 0 || lci[a] >= nbr)
+                return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: column out of range in row %lld", (long long)I);
     }
+    const int64_t np = plan->n_panels;
+    std::vector<int64_t> cnt(np), nrow(np), ent_off(np + 1), lrow_base(np + 1);
+    std::vector<int32_t> lrow_ptr;
+    std::vector<uint32_t> lent;
+    const int nth = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)std::thread::hardware_concurrency(), 16, np}));
+    auto run = [&](bool count_only) {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nth; ++t) {
+            const int64_t p0 = np * t / nth, p1 = np * (t + 1) / nth;
+            th.emplace_back([&, p0, p1] {
+                build_row_lists(plan, rp, ci, lrp, lci, p0, p1, count_only, cnt, nrow, ent_off, lrow_ptr, lrow_base,
+                                lent);
+            });
+        }
+        for (auto &x : th) x.join();
+    };
+    run(true);
+    ent_off[0] = lrow_base[0] = 0;
+    for (int64_t p = 0; p < np; ++p) {
+        ent_off[p + 1] = ent_off[p] + cnt[p];
+        lrow_base[p + 1] = lrow_base[p] + nrow[p];
+    }
+    if (ent_off[np] >= (int64_t)INT32_MAX)
+        return fail(CHEB_ERR_NOSPACE, "cheb_plan_attach_operator: %lld list entries exceed the int32 offsets",
+                    (long long)ent_off[np]);
+    lrow_ptr.resize(lrow_base[np]);
+    lent.resize(ent_off[np]);
+    run(false);
+    lrow_base.resize(np);
     plan->op_rp = L->row_ptr;
     plan->op_ci = L->col_idx;
-    plan->n_pairs = (int64_t)pair_rows.size() / 2;
-    plan->n_entries = (int64_t)ent_s.size();
-    plan->h_pair_ptr.swap(pair_ptr);
-    plan->h_pair_rows.swap(pair_rows);
-    plan->h_ent_ptr.swap(ent_ptr);
-    plan->h_ent_a.swap(ent_a);
-    plan->h_ent_s.swap(ent_s);
-    plan->op_ws_bytes = align_up(plan->h_pair_ptr.size() * 4) + align_up(plan->h_pair_rows.size() * 4) +
-                        align_up(plan->h_ent_ptr.size() * 4) + align_up(plan->h_ent_a.size() * 4) +
-                        align_up(plan->h_ent_s.size() * 2);
+    plan->n_list_rows = (int64_t)lrow_ptr.size();
+    plan->n_entries = (int64_t)lent.size();
+    plan->h_lrow_base.swap(lrow_base);
+    plan->h_lrow_ptr.swap(lrow_ptr);
+    plan->h_lent.swap(lent);
+    plan->op_ws_bytes = align_up(plan->h_lrow_base.size() * 8) + align_up(plan->h_lrow_ptr.size() * 4) +
+                        align_up(std::max<size_t>(plan->h_lent.size(), 1) * 4);
     plan->op_bound = false;
     *op_ws_bytes = plan->op_ws_bytes;
     return CHEB_OK;
@@ -351,21 +388,21 @@ extern "C" int cheb_plan_bind_operator(cheb_plan *plan, void *ws, size_t ws_byte
         return fail(CHEB_ERR_NOSPACE, "cheb_plan_bind_operator: workspace %zu < %zu or misaligned", ws_bytes,
                     plan->op_ws_bytes);
     Carve cv(ws, ws_bytes);
-    plan->d_pair_ptr = cv.take<int32_t>(plan->h_pair_ptr.size());
-    plan->d_pair_rows = cv.take<int32_t>(plan->h_pair_rows.size());
-    plan->d_ent_ptr = cv.take<int32_t>(plan->h_ent_ptr.size());
-    plan->d_ent_a = cv.take<int32_t>(plan->h_ent_a.size());
-    plan->d_ent_s = cv.take<uint16_t>(plan->h_ent_s.size());
+    plan->d_lrow_base = cv.take<int64_t>(plan->h_lrow_base.size());
+    plan->d_lrow_ptr = cv.take<int32_t>(plan->h_lrow_ptr.size());
+    plan->d_lent = cv.take<uint32_t>(std::max<size_t>(plan->h_lent.size(), 1));
     cudaStream_t s = as_stream(stream);
-    CHEB_CUDA(cudaMemcpyAsync(plan->d_pair_ptr, plan->h_pair_ptr.data(), plan->h_pair_ptr.size() * 4, cudaMemcpyHostToDevice, s));
-    CHEB_CUDA(cudaMemcpyAsync(plan->d_pair_rows, plan->h_pair_rows.data(), plan->h_pair_rows.size() * 4, cudaMemcpyHostToDevice, s));
-    CHEB_CUDA(cudaMemcpyAsync(plan->d_ent_ptr, plan->h_ent_ptr.data(), plan->h_ent_ptr.size() * 4, cudaMemcpyHostToDevice, s));
-    CHEB_CUDA(cudaMemcpyAsync(plan->d_ent_a, plan->h_ent_a.data(), plan->h_ent_a.size() * 4, cudaMemcpyHostToDevice, s));
-    CHEB_CUDA(cudaMemcpyAsync(plan->d_ent_s, plan->h_ent_s.data(), plan->h_ent_s.size() * 2, cudaMemcpyHostToDevice, s));
+    CHEB_CUDA(cudaMemcpyAsync(plan->d_lrow_base, plan->h_lrow_base.data(), plan->h_lrow_base.size() * 8,
+                              cudaMemcpyHostToDevice, s));
+    CHEB_CUDA(cudaMemcpyAsync(plan->d_lrow_ptr, plan->h_lrow_ptr.data(), plan->h_lrow_ptr.size() * 4,
+                              cudaMemcpyHostToDevice, s));
+    if (!plan->h_lent.empty())
+        CHEB_CUDA(cudaMemcpyAsync(plan->d_lent, plan->h_lent.data(), plan->h_lent.size() * 4, cudaMemcpyHostToDevice,
+                                  s));
     CHEB_CUDA(cudaStreamSynchronize(s));
     // the device copies are the only ones needed from here on
-    std::vector<int32_t>().swap(plan->h_ent_a);
-    std::vector<uint16_t>().swap(plan->h_ent_s);
+    std::vector<int32_t>().swap(plan->h_lrow_ptr);
+    std::vector<uint32_t>().swap(plan->h_lent);
     plan->op_bound = true;
     return CHEB_OK;
 }

@@ -42,28 +42,32 @@ struct cheb_plan {
     int32_t *d_rpanel_sys = nullptr;
     int32_t *d_sys_rpanel = nullptr;
     size_t ws_bytes = 0;
-    // Operator pair lists (cheb_plan_attach_operator): for every step panel, its
-    // union rows taken two at a time, and for each pair the merged list of the
-    // operator's in-union blocks: (block of row 1 or -1, block of row 2 or -1,
-    // union slot of K).  Valid for the operator pattern (op_rp, op_ci) only.
+    // Operator row lists (cheb_plan_attach_operator): for every step panel and
+    // each of its union rows (ascending block row), the operator row's blocks
+    // whose column lies in the union, as (offset of the block in the operator
+    // row << 16 | union slot of the column).  Valid for the operator pattern
+    // (op_rp, op_ci) only.
     const int64_t *op_rp = nullptr;
     const int32_t *op_ci = nullptr;
-    int64_t n_pairs = 0, n_entries = 0;
-    std::vector<int32_t> h_pair_ptr;   // [n_panels + 1]
-    std::vector<int32_t> h_pair_rows;  // [2 * n_pairs] union slots (second -1 if alone)
-    std::vector<int32_t> h_ent_ptr;    // [n_pairs + 1]
-    std::vector<int32_t> h_ent_a;      // [2 * n_entries]
-    std::vector<uint16_t> h_ent_s;     // [n_entries]
+    int64_t n_list_rows = 0, n_entries = 0;
+    std::vector<int64_t> h_lrow_base;  // [n_panels] first row pointer of each panel
+    std::vector<int32_t> h_lrow_ptr;   // [sum of (union + 1) over panels] entry offsets
+    std::vector<uint32_t> h_lent;      // [n_entries]
     size_t op_ws_bytes = 0;
     bool op_bound = false;
-    int32_t *d_pair_ptr = nullptr, *d_pair_rows = nullptr, *d_ent_ptr = nullptr, *d_ent_a = nullptr;
-    uint16_t *d_ent_s = nullptr;
+    int64_t *d_lrow_base = nullptr;
+    int32_t *d_lrow_ptr = nullptr;
+    uint32_t *d_lent = nullptr;
 };
 
 namespace cheb {
 
 // Shared-memory layout of the step kernel for a panel of width P over a union of
 // ucap rows, element size esz, nw bitmap words, nwarps warps.
+// Operator blocks per staged batch of the step kernel: 16 for panels of two or
+// more columns (a multiple of the 32/P K-groups of a warp), 32 for one column.
+__host__ __device__ constexpr int step_batch(int P) { return P >= 2 ? 16 : 32; }
+
 struct StepLayout {
     size_t off_bits, off_ulist, off_pos, off_wl, off_bslot, off_hbuf, off_x, off_red, total;
 };
@@ -78,7 +82,7 @@ __host__ __device__ inline StepLayout step_layout(int64_t nw, int64_t ucap, int 
     o += (size_t)ucap * 4;
     o = (o + 15) / 16 * 16;
     L.off_pos = o;
-    o += (size_t)ucap * P * 2;  // int16 position of the row within each panel column
+    o += (size_t)ucap * P * 4;  // output block index of (union row, panel column), -1 if absent
     o = (o + 15) / 16 * 16;
     L.off_wl = o;
     o += (size_t)nwarps * 64 * 8;  // per-warp ring of staged (block index, union slot) pairs
@@ -86,7 +90,7 @@ __host__ __device__ inline StepLayout step_layout(int64_t nw, int64_t ucap, int 
     o += (size_t)nwarps * 64 * 4;  // union slots of the two staged batches
     o = (o + 127) / 128 * 128;
     L.off_hbuf = o;
-    o += (size_t)nwarps * 2 * 32 * BB * esz;  // two batches of 32 operator blocks per warp
+    o += (size_t)nwarps * 2 * step_batch(P) * BB * esz;  // two staged batches of operator blocks per warp
     o = (o + 15) / 16 * 16;
     L.off_x = o;
     o += (size_t)ucap * BB * P * esz;  // the gathered panel of T_k

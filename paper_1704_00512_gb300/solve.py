@@ -40,7 +40,7 @@ class Problem:
     """Device-resident inputs of one system: atoms, P_H with S and H, and P_out."""
 
     def __init__(self, xyz: np.ndarray, L_box: float, r_c: float, r_buf: float, S_vals: np.ndarray,
-                 H_vals: np.ndarray, device, precision: int = L.F64):
+                 H_vals: np.ndarray, device, precision: int = L.F64, op_lists: bool = True):
         self.device = torch.device(device)
         self.L = float(L_box)
         self.r_c = float(r_c)
@@ -49,6 +49,7 @@ class Problem:
         self.S_host = S_vals
         self.H_host = H_vals
         self.precision = precision
+        self.op_lists = op_lists
         self.build_patterns()
         self.S = self.P_H.with_vals(torch.as_tensor(np.ascontiguousarray(S_vals), dtype=torch.float64,
                                                     device=self.device))
@@ -62,6 +63,11 @@ class Problem:
         self.P_out = L.Bsr(rp, ci)
         self.plan64 = L.Plan(self.P_out, L.F64)
         self.planX = self.plan64 if self.precision == L.F64 else L.Plan(self.P_out, self.precision)
+        if self.op_lists:
+            # gather plan of the recursions on S~ and H~' (both on P_H)
+            self.plan64.attach_operator(self.P_H)
+            if self.planX is not self.plan64:
+                self.planX.attach_operator(self.P_H)
 
     @property
     def n_rows(self) -> int:
@@ -71,8 +77,8 @@ class Problem:
         return torch.zeros((self.P_out.nnzb, 4, 4), dtype=torch.float64, device=self.device)
 
 
-def problem_from_system(sysm, r_buf: float, device, precision: int = L.F64) -> Problem:
-    return Problem(sysm.xyz, sysm.L, sysm.r_cut, r_buf, sysm.S, sysm.H, device, precision)
+def problem_from_system(sysm, r_buf: float, device, precision: int = L.F64, op_lists: bool = True) -> Problem:
+    return Problem(sysm.xyz, sysm.L, sysm.r_cut, r_buf, sysm.S, sysm.H, device, precision, op_lists)
 
 
 def powers(pb: Problem, exponents=(-1.0, 0.5, -0.5), tol: float = 1e-10, n_max: int = 512,
@@ -137,14 +143,11 @@ def postprocess(pb: Problem, A: torch.Tensor, p: torch.Tensor) -> torch.Tensor:
 def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FERMI, n_max: int = 16384,
         lanczos_k: int = 40, tol_N: float | None = None, bounds_S=None, n_S=None, bounds_H=None, n_H=None,
         max_iter: int = 100, n_mu: int = 1, mu_stencil: float = 0.05, tol_S: float | None = None,
-        stepwise: bool = True, isqrt: str = "f64", pair_lists: bool = False, timings: dict | None = None) -> dict:
+        stepwise: bool = True, isqrt: str = "f64", timings: dict | None = None) -> dict:
     """Density matrix F with Tr(F S) = N_e (see the module docstring for the steps).
 
     isqrt: "f64" expands S^-1/2 in FP64; "f32ns" expands it in the problem's
     reduced precision and applies one FP64 Newton-Schulz correction.
-    pair_lists: precompute the H~' pair lists for the per-step kernel
-    (cheb_plan_attach_operator); measured slower on GB300 (5.6 vs 4.9 ms per
-    FP32 step at 40k rows), so off by default.
     """
     tm = {} if timings is None else timings
     t0 = time.perf_counter()
@@ -162,8 +165,6 @@ def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FE
     else:
         e0, e1 = bounds_H
     Hpt = Hp.with_vals(L.scale(Hp, e0, e1))
-    if stepwise and pair_lists:
-        pb.planX.attach_operator(Hpt)
     G = trace_functional(pb, A)
     mid = 0.5 * (e0 + e1)
     if n_H is None:

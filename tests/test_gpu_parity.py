@@ -488,27 +488,61 @@ def test_mixed_precision_error_at_the_bench_degree():
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_operator_pair_lists_match_oracle(prec):
+def test_operator_row_lists_match_oracle_and_ranking_path(prec):
     n, nf = 40, 2
     for n_atoms, r_c, r_buf in ((33, 3.0, 1.5), (300, 6.0, 3.0)):
         s, H, P_out, e0, e1, Ht, coeffs, G = _expand_case(n_atoms, r_c, r_buf, 51 + n_atoms, n, nf)
         ex = ref.chebyshev_expand(Ht, P_out, coeffs, G=G)
         dP = dbsr(P_out.row_ptr, P_out.col_idx)
         dHt = dbsr(Ht.row_ptr, Ht.col_idx, Ht.vals)
-        plan = cg.Plan(dP, prec).attach_operator(dHt)
-        acc = [torch.zeros((P_out.nnzb, 4, 4), dtype=torch.float64, device=DEV) for _ in range(nf)]
-        g = torch.zeros(n, dtype=torch.float64, device=DEV)
-        cg.expand(plan, dHt, n, torch.as_tensor(coeffs, device=DEV), acc, G=torch.as_tensor(G.vals, device=DEV),
-                  gmoments=g, precision=prec, stepwise=True)
+        dc = torch.as_tensor(coeffs, device=DEV)
+        dG = torch.as_tensor(G.vals, device=DEV)
+
+        def run(plan):
+            acc = [torch.zeros((P_out.nnzb, 4, 4), dtype=torch.float64, device=DEV) for _ in range(nf)]
+            g = torch.zeros(n, dtype=torch.float64, device=DEV)
+            cg.expand(plan, dHt, n, dc, acc, G=dG, gmoments=g, precision=prec, stepwise=True)
+            return acc, g
+
+        acc_rank, g_rank = run(cg.Plan(dP, prec))
+        acc, g = run(cg.Plan(dP, prec).attach_operator(dHt))
         tol = 1e-10 if prec == cg.F64 else 1e-5
         for j in range(nf):
             assert relF(acc[j].cpu().numpy(), ex.acc[j].vals) < tol
+            # same blocks multiplied in the same order as the ranking path
+            assert torch.equal(acc[j], acc_rank[j])
         assert relF(g.cpu().numpy(), ex.g) < tol
-        # an operator with another pattern takes the general path on the same plan
-        dH = dbsr(H.row_ptr, H.col_idx, H.vals)
-        R = torch.as_tensor(np.random.default_rng(1).normal(size=(P_out.nnzb, 4, 4)), device=DEV)
-        if prec == cg.F64:
-            C = torch.empty_like(R)
-            cg.masked_product(plan, cg.Bsr(dH.row_ptr.clone(), dH.col_idx.clone(), dH.vals), R, C)
-            want = ref.masked_product(H, P_out.with_vals(R.cpu().numpy()), P_out.row_ptr, P_out.col_idx)
-            assert relF(C.cpu().numpy(), want) < 1e-13
+        assert torch.equal(g, g_rank)
+
+
+@pytest.mark.parametrize("n_atoms,r_c,r_buf", [(33, 3.0, 1.5), (150, 5.0, 3.0), (600, 8.0, 4.0)])
+def test_masked_product_row_lists(n_atoms, r_c, r_buf):
+    """Masked products through the row lists, including an operator whose rows
+    have no block inside some panels' unions, and an operator of another
+    pattern on the same plan (ranking path)."""
+    s, S, H, P_out = setup(n_atoms, r_c, r_buf, n_atoms)
+    rng = np.random.default_rng(n_atoms + 7)
+    R = torch.as_tensor(rng.normal(size=(P_out.nnzb, 4, 4)), device=DEV)
+    dP = dbsr(P_out.row_ptr, P_out.col_idx)
+    # a sparse operator on P_H: only blocks with (I + K) % 3 == 0 kept, so some
+    # rows have none in a panel's union
+    keep_rows = [[k for k in range(H.row_ptr[i], H.row_ptr[i + 1]) if (i + H.col_idx[k]) % 3 == 0]
+                 for i in range(H.nbr)]
+    rp = np.zeros(H.nbr + 1, dtype=np.int64)
+    rp[1:] = np.cumsum([len(r) for r in keep_rows])
+    ks = np.array([k for r in keep_rows for k in r], dtype=np.int64)
+    Ls = ref.Bsr(rp, H.col_idx[ks], rng.normal(size=(len(ks), 4, 4)))
+    for Lm in (H, Ls):
+        dL = dbsr(Lm.row_ptr, Lm.col_idx, Lm.vals)
+        plan = cg.Plan(dP, cg.F64).attach_operator(dL)
+        C = torch.empty_like(R)
+        cg.masked_product(plan, dL, R, C)
+        want = ref.masked_product(Lm, P_out.with_vals(R.cpu().numpy()), P_out.row_ptr, P_out.col_idx)
+        assert relF(C.cpu().numpy(), want) < 1e-13
+        # another operator pattern on the same plan takes the ranking path
+        dO = dbsr(P_out.row_ptr, P_out.col_idx, rng.normal(size=(P_out.nnzb, 4, 4)))
+        C2 = torch.empty_like(R)
+        cg.masked_product(plan, dO, R, C2)
+        want2 = ref.masked_product(ref.Bsr(P_out.row_ptr, P_out.col_idx, dO.vals.cpu().numpy()),
+                                   P_out.with_vals(R.cpu().numpy()), P_out.row_ptr, P_out.col_idx)
+        assert relF(C2.cpu().numpy(), want2) < 1e-13
