@@ -11,11 +11,16 @@
 //      32/P K-groups; a lane accumulates the full 4x4 block sum over K of
 //      M~_IK X[K] for its column -- the masked product restricted to the
 //      panel's columns (columns are independent, Sec. "Expansion in Chebyshev
-//      polynomials");
-//   4. K-groups are summed by butterfly shuffles, then the epilogue writes
-//      T_{k+1} = alpha * (M~ T_k) + beta * T_{k-1} for the blocks of P_out only
-//      (the truncation, Sec. "Sparsity and truncation"), adds c_j[k+1] T_{k+1}
-//      to every FP64 accumulator j, and sums Tr T_{k+1} and <T_{k+1}, G>;
+//      polynomials").  The operator blocks M~_IK with K in the union come from
+//      the plan's per-panel row lists, or from ranking the operator row's
+//      column indices against the union bitmap;
+//   4. when a row is done the K-groups' sums are combined by a reduce-scatter;
+//      for the blocks of P_out only (the truncation, Sec. "Sparsity and
+//      truncation") T_{k+1} = alpha * (M~ T_k) + beta * T_{k-1} is formed,
+//      c_j[k+1] T_{k+1} added to every FP64 accumulator j, and Tr T_{k+1} and
+//      <T_{k+1}, G> summed -- by each lane for its elements as soon as the row
+//      is done (FP64), or in a pass over the panel's blocks after all rows
+//      (FP32, whose latency-bound rows gain from many loads in flight);
 //   5. the last thread block to finish sums the per-block moment partials in
 //      a fixed order (deterministic) and resets the completion counter.
 #include <cuda_bf16.h>
@@ -70,7 +75,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
     constexpr int KG = 32 / P;                  // K-groups per warp
     constexpr int BT = step_batch(P);          // operator blocks per staged batch
     constexpr int NU = BT / KG;                 // staged entries per K-group per batch
-    constexpr int EPL = KG >= 16 ? 1 : 16 / KG;  // raw-store elements per lane
+    constexpr int EPL = KG >= 16 ? 1 : 16 / KG;  // elements of a block sum per lane
+    // FP64 rows are bound by the FMA pipe, which hides the memory latency of
+    // finishing each row at once; FP32 rows are latency-bound and finish in a
+    // separate pass over the panel's blocks with many loads in flight.
+    constexpr bool FUSE = sizeof(T) == 8;
     const StepLayout lay = step_layout(a.nw, a.ucap, P, sizeof(T), NW);
     uint2 *bits = reinterpret_cast<uint2 *>(smem + lay.off_bits);
     int32_t *ulist = reinterpret_cast<int32_t *>(smem + lay.off_ulist);
@@ -139,6 +148,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
     }
     __syncthreads();
 
+    double coefv[MAX_F];
+#pragma unroll
+    for (int f = 0; f < MAX_F; ++f) coefv[f] = f < a.nf ? a.coef[(int64_t)f * a.coef_stride + a.term] : 0.0;
+    double tpart = 0.0, gpart = 0.0;
+
     // 3. union rows: masked block products M~_I. X for the panel's columns.
     // Each warp takes union rows s = warp, warp + NW, ...; the in-union
     // operator blocks of its rows form one stream of batches of up to BT.  A
@@ -189,19 +203,84 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
                 }
             }
         };
+        // A finished row: the K-groups' partial 4x4 sums are combined by a
+        // reduce-scatter -- plain butterflies over K-group bits beyond 16
+        // groups, then halving exchanges from the highest K-group bit down --
+        // after which the lane holds elements i0 .. i0+EPL-1 of the block sum,
+        // i0 = (kg >> EX) * EPL, of the output block (row ulist[s], column
+        // j0 + q) if P_out has it.  With FUSE the lane finishes them at once:
+        // T_{k+1} = alpha * (M~ T_k) + beta * T_{k-1}, every FP64 accumulator
+        // += c_j[k+1] T_{k+1}, and its parts of Tr T_{k+1} and <T_{k+1}, G>;
+        // otherwise it stores the raw sum for the epilogue pass (step 4).
+        constexpr int LKG = ilog2(KG), EX = LKG > 4 ? LKG - 4 : 0, LV = LKG - EX;
         auto finish_row = [&](T(&acc)[16], int s) {
 #pragma unroll
-            for (int o = P; o < 32; o <<= 1)
+            for (int t = 0; t < EX; ++t)
 #pragma unroll
-                for (int i = 0; i < 16; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
-            // raw product into the output slot; the epilogue below finishes it
-            if (q < ncols && kg * EPL < 16) {
-                const int e = oslot[s * P + q];
-                if (e >= 0) {
-                    const int64_t slot = (int64_t)e * BB;
+                for (int i = 0; i < 16; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], P << t);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (i / EPL == kg) a.C[slot + i] = acc[i];
+            for (int l = 0; l < LV; ++l) {
+                const int bit = LKG - 1 - l, n = 16 >> (l + 1);
+                const bool hi = (kg >> bit) & 1;
+#pragma unroll
+                for (int j = 0; j < n; ++j) {
+                    const T mine = hi ? acc[n + j] : acc[j], other = hi ? acc[j] : acc[n + j];
+                    acc[j] = mine + __shfl_xor_sync(0xffffffffu, other, P << bit);
+                }
+            }
+            const int o = q < ncols && (kg & ((1 << EX) - 1)) == 0 ? oslot[s * P + q] : -1;
+            if (!FUSE && o >= 0) {
+                // raw product; the epilogue pass below finishes the block
+                T y[EPL];
+#pragma unroll
+                for (int j = 0; j < EPL; ++j) y[j] = acc[j];
+                stn<T, EPL>(a.C + (int64_t)o * BB + (kg >> EX) * EPL, y);
+            }
+            if (FUSE && o >= 0) {
+                const int i0 = (kg >> EX) * EPL;
+                const int64_t idx = (int64_t)o * BB + i0;
+                T y[EPL];
+                if (a.Rm) {
+                    T m[EPL];
+                    ldgn<T, EPL>(m, a.Rm + idx);
+#pragma unroll
+                    for (int j = 0; j < EPL; ++j) y[j] = a.alpha * acc[j] + a.beta * m[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < EPL; ++j) y[j] = a.alpha * acc[j];
+                }
+                if (a.round_bf16) {
+#pragma unroll
+                    for (int j = 0; j < EPL; ++j) y[j] = bf16_round(y[j]);
+                }
+                stn<T, EPL>(a.C + idx, y);
+                double yd[EPL];
+#pragma unroll
+                for (int j = 0; j < EPL; ++j) yd[j] = (double)y[j];
+                // all accumulators are loaded before any is written back, so
+                // their loads are in flight together
+                double av[MAX_F][EPL];
+#pragma unroll
+                for (int f = 0; f < MAX_F; ++f)
+                    if (f < a.nf) ldn<double, EPL>(av[f], a.acc[f] + idx);
+#pragma unroll
+                for (int f = 0; f < MAX_F; ++f) {
+                    if (f < a.nf) {
+#pragma unroll
+                        for (int j = 0; j < EPL; ++j) av[f][j] += coefv[f] * yd[j];
+                        stn<double, EPL>(a.acc[f] + idx, av[f]);
+                    }
+                }
+                if (a.G) {
+                    double gv[EPL];
+                    ldgn<double, EPL>(gv, a.G + idx);
+#pragma unroll
+                    for (int j = 0; j < EPL; ++j) gpart += gv[j] * yd[j];
+                }
+                if (ulist[s] == j0 + q) {
+#pragma unroll
+                    for (int j = 0; j < EPL; ++j)
+                        if ((i0 + j) % 5 == 0) tpart += yd[j];  // diagonal elements 0, 5, 10, 15
                 }
             }
 #pragma unroll
@@ -388,76 +467,75 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
     }
     __syncthreads();
 
-    // 4. epilogue over the panel's output blocks, one block row (4 elements) per
-    // thread in column order: T_{k+1} = alpha * (M~ T_k) + beta * T_{k-1},
-    // accumulators, Tr T_{k+1} and <T_{k+1}, G>.
-    double coefv[MAX_F];
+    // 4. without FUSE, the epilogue pass over the panel's output blocks, one
+    // block row (4 elements) per thread in column order: T_{k+1} = alpha *
+    // (M~ T_k) + beta * T_{k-1}, accumulators, Tr T_{k+1} and <T_{k+1}, G>.
+    if constexpr (!FUSE) {
+        // cumulative block counts of the panel's columns (indexed by constants only)
+        int cum[5];
+        cum[0] = 0;
+        int nblk = 0;
 #pragma unroll
-    for (int f = 0; f < MAX_F; ++f) coefv[f] = f < a.nf ? a.coef[(int64_t)f * a.coef_stride + a.term] : 0.0;
-    // cumulative block counts of the panel's columns (indexed by constants only)
-    int cum[5];
-    cum[0] = 0;
-    int nblk = 0;
+        for (int q = 0; q < 4; ++q) {
+            cum[q + 1] = cum[q] + (q < ncols ? (int)(a.rp[j0 + q + 1] - a.rp[j0 + q]) : 0);
+            if (q < ncols) nblk = cum[q + 1];
+        }
+        for (int t = tid; t < nblk * 4; t += NT) {
+            const int b = t >> 2, r = t & 3;
+            int q = 0, base = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        cum[q + 1] = cum[q] + (q < ncols ? (int)(a.rp[j0 + q + 1] - a.rp[j0 + q]) : 0);
-        if (q < ncols) nblk = cum[q + 1];
-    }
-    double tpart = 0.0, gpart = 0.0;
-    for (int t = tid; t < nblk * 4; t += NT) {
-        const int b = t >> 2, r = t & 3;
-        int q = 0, base = 0;
+            for (int qq = 1; qq < 4; ++qq)
+                if (qq < ncols && b >= cum[qq]) {
+                    q = qq;
+                    base = cum[qq];
+                }
+            const int J = j0 + q;
+            const int64_t p = a.rp[J] + (b - base);
+            const int K = a.ci[p];
+            const int64_t idx = (int64_t)a.tperm[p] * BB + 4 * r;
+            T y[4];
+            Vec4<T>::ld(y, a.C + idx);
+            if (a.Rm) {
+                T m4[4];
+                Vec4<T>::ldg(m4, a.Rm + idx);
 #pragma unroll
-        for (int qq = 1; qq < 4; ++qq)
-            if (qq < ncols && b >= cum[qq]) {
-                q = qq;
-                base = cum[qq];
+                for (int c = 0; c < 4; ++c) y[c] = a.alpha * y[c] + a.beta * m4[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) y[c] = a.alpha * y[c];
             }
-        const int J = j0 + q;
-        const int64_t p = a.rp[J] + (b - base);
-        const int K = a.ci[p];
-        const int64_t idx = (int64_t)a.tperm[p] * BB + 4 * r;
-        T y[4];
-        Vec4<T>::ld(y, a.C + idx);
-        if (a.Rm) {
-            T m4[4];
-            Vec4<T>::ldg(m4, a.Rm + idx);
+            if (a.round_bf16) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) y[c] = a.alpha * y[c] + a.beta * m4[c];
-        } else {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) y[c] = a.alpha * y[c];
-        }
-        if (a.round_bf16) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) y[c] = bf16_round(y[c]);
-        }
-        Vec4<T>::st(a.C + idx, y);
-        double yd[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) yd[c] = (double)y[c];
-        // all accumulator rows are loaded before any is written back, so their
-        // loads are in flight together
-        double av[MAX_F][4];
-#pragma unroll
-        for (int f = 0; f < MAX_F; ++f)
-            if (f < a.nf) Vec4<double>::ld(av[f], a.acc[f] + idx);
-#pragma unroll
-        for (int f = 0; f < MAX_F; ++f) {
-            if (f < a.nf) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) av[f][c] += coefv[f] * yd[c];
-                Vec4<double>::st(a.acc[f] + idx, av[f]);
+                for (int c = 0; c < 4; ++c) y[c] = bf16_round(y[c]);
             }
-        }
-        if (a.G) {
-            double gv[4];
-            Vec4<double>::ldg(gv, a.G + idx);
+            Vec4<T>::st(a.C + idx, y);
+            double yd[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) gpart += gv[c] * yd[c];
+            for (int c = 0; c < 4; ++c) yd[c] = (double)y[c];
+            // all accumulator rows are loaded before any is written back, so
+            // their loads are in flight together
+            double av[MAX_F][4];
+#pragma unroll
+            for (int f = 0; f < MAX_F; ++f)
+                if (f < a.nf) Vec4<double>::ld(av[f], a.acc[f] + idx);
+#pragma unroll
+            for (int f = 0; f < MAX_F; ++f) {
+                if (f < a.nf) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) av[f][c] += coefv[f] * yd[c];
+                    Vec4<double>::st(a.acc[f] + idx, av[f]);
+                }
+            }
+            if (a.G) {
+                double gv[4];
+                Vec4<double>::ldg(gv, a.G + idx);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) gpart += gv[c] * yd[c];
+            }
+            if (K == J) tpart += yd[r];
         }
-        if (K == J) tpart += yd[r];
     }
+    // 5. the moment partials of the panel
     if (a.mom || a.gmom) {
         Moments<2> mm{{tpart, gpart}, {a.mom, a.gmom}};
         finish_moments<NT, 2>(a.part, a.counter, mm, red);

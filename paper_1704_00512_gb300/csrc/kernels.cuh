@@ -194,6 +194,56 @@ struct Vec4<double> {
 };
 
 
+// N = 1, 2 or 4 consecutive elements at p (aligned to N elements): plain load,
+// read-only load and store.
+template <typename T, int N>
+__device__ __forceinline__ void ldn(T (&v)[N], const T *p) {
+    if constexpr (N == 4) {
+        Vec4<T>::ld(v, p);
+    } else if constexpr (N == 2) {
+        if constexpr (sizeof(T) == 4) {
+            const float2 a = *reinterpret_cast<const float2 *>(p);
+            v[0] = a.x; v[1] = a.y;
+        } else {
+            const double2 a = *reinterpret_cast<const double2 *>(p);
+            v[0] = a.x; v[1] = a.y;
+        }
+    } else {
+        v[0] = *p;
+    }
+}
+template <typename T, int N>
+__device__ __forceinline__ void ldgn(T (&v)[N], const T *p) {
+    if constexpr (N == 4) {
+        Vec4<T>::ldg(v, p);
+    } else if constexpr (N == 2) {
+        if constexpr (sizeof(T) == 4) {
+            const float2 a = __ldg(reinterpret_cast<const float2 *>(p));
+            v[0] = a.x; v[1] = a.y;
+        } else {
+            const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+            v[0] = a.x; v[1] = a.y;
+        }
+    } else {
+        v[0] = __ldg(p);
+    }
+}
+template <typename T, int N>
+__device__ __forceinline__ void stn(T *p, const T (&v)[N]) {
+    if constexpr (N == 4) {
+        Vec4<T>::st(p, v);
+    } else if constexpr (N == 2) {
+        if constexpr (sizeof(T) == 4)
+            *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+        else
+            *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    } else {
+        *p = v[0];
+    }
+}
+
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
+
 // Byte offset of 16-byte chunk c of panel block b (XOR-swizzled inside its
 // 128-byte line so 32 lanes reading chunk c of 32 blocks spread over the banks).
 template <typename T>
