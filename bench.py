@@ -155,6 +155,38 @@ def measured_hbm_peak() -> tuple[float, str]:
 
 
 # --------------------------------------------------------------------------
+# ranks: each rank solves its own seeded system (no data-path collective); the
+# timed region is bracketed by barriers and the job time is the max over ranks
+# --------------------------------------------------------------------------
+
+def rank_env() -> tuple[int, int, int]:
+    """(rank, world size, local rank) from the torchrun environment (1 process by default)."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def system_seed(rank: int) -> int:
+    """Seed of the system a rank solves: independent systems, weak scaling."""
+    return rank
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over all ranks (x itself for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(steps: int, world: int, t_ms: float) -> float:
+    """Whole-job solves/s: every rank solved `steps` systems within the max time t_ms."""
+    return steps * world / (t_ms / 1e3)
+
+
+# --------------------------------------------------------------------------
 # the CUDA arm
 # --------------------------------------------------------------------------
 
@@ -173,7 +205,7 @@ def run_cheb(args, rank: int, world: int, local: int):
     cfg = WORKLOADS[args.workload]
     prec = cg.F32 if cfg["precision"] == "f32" else cg.F64
     t0 = time.time()
-    sysm = synth.make_system(cfg["n_atoms"], cfg["r_c"], seed=rank)
+    sysm = synth.make_system(cfg["n_atoms"], cfg["r_c"], seed=system_seed(rank))
     log(f"[rank {rank}] generated {sysm.n_rows} rows, {sysm.nnzb} blocks in {time.time() - t0:.1f}s")
     pb = solve.problem_from_system(sysm, cfg["r_buf"], dev, prec)
     kw = dict(kT=cfg["kT"], N_e=cfg["N_e"], tol=cfg["tol"], tol_S=cfg["tol_S"], n_mu=cfg["n_mu"])
@@ -216,11 +248,8 @@ def run_cheb(args, rank: int, world: int, local: int):
                             pb.P_out.row_ptr.cpu().numpy(), pb.P_out.col_idx.cpu().numpy())
     p1 = sum(ev[0].elapsed_time(ev[1]) for ev in pass_ms) / args.steps
     p2 = sum(ev[2].elapsed_time(ev[3]) for ev in pass_ms) / args.steps
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = args.steps * world / (t_ms / 1e3)
+    t_ms = max_over_ranks(t_ms, world, dev)
+    value = job_throughput(args.steps, world, t_ms)
 
     # ---- end-to-end through the same API from pinned host buffers
     h_xyz = torch.from_numpy(np.ascontiguousarray(sysm.xyz)).pin_memory()
@@ -245,11 +274,8 @@ def run_cheb(args, rank: int, world: int, local: int):
     f1.record()
     torch.cuda.synchronize()
     te_ms = f0.elapsed_time(f1)
-    if world > 1:
-        tt = torch.tensor([te_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te_ms = float(tt.item())
-    e2e_value = args.e2e_steps * world / (te_ms / 1e3)
+    te_ms = max_over_ranks(te_ms, world, dev)
+    e2e_value = job_throughput(args.e2e_steps, world, te_ms)
 
     # ---- roofline of the dominant kernel (the fused recursion step)
     esz = 4 if prec == cg.F32 else 8
@@ -387,9 +413,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         log("note: fewer than 3 warm-up steps")
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = rank_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -185,6 +185,33 @@ def test_expand_fp32_error_bound():
         assert relF(acc[j].cpu().numpy(), ex.acc[j].vals) < 1e-4
 
 
+def test_expand_bf16_error_bound():
+    # BF16 mode: M~ and every stored T_k rounded to bfloat16 (u = 2^-8), block
+    # products summed in FP32, accumulators and moments in FP64.  The same
+    # perturbation argument as for FP32 bounds the error with u = 2^-8.
+    n, nf = 64, 2
+    s, H, P_out, e0, e1, Ht, coeffs, G = _expand_case(150, 4.0, 2.0, 9, n, nf)
+    ex = ref.chebyshev_expand(Ht, P_out, coeffs, G=G)
+    dP = dbsr(P_out.row_ptr, P_out.col_idx)
+    plan = cg.Plan(dP, cg.BF16)
+    dHt = dbsr(Ht.row_ptr, Ht.col_idx, Ht.vals)
+    acc = [torch.zeros((P_out.nnzb, 4, 4), dtype=torch.float64, device=DEV) for _ in range(nf)]
+    g = torch.zeros(n, dtype=torch.float64, device=DEV)
+    cg.expand(plan, dHt, n, torch.as_tensor(coeffs, device=DEV), acc, G=torch.as_tensor(G.vals, device=DEV),
+              gmoments=g, precision=cg.BF16, stepwise=True)
+    u = 2.0 ** -8
+    k = np.arange(n)
+    errs = []
+    for j in range(nf):
+        bound = 8 * u * np.sum(np.abs(coeffs[j]) * (1 + k) ** 2) * np.sqrt(P_out.nnzb * 16)
+        err = np.linalg.norm(acc[j].cpu().numpy() - ex.acc[j].vals)
+        errs.append(relF(acc[j].cpu().numpy(), ex.acc[j].vals))
+        assert err < bound, (err, bound)
+    print(f"BF16 recursion, {n} terms: relative Frobenius error of the accumulators {max(errs):.2e}")
+    # bfloat16 really is coarser than FP32 here, and still a usable approximation
+    assert 1e-5 < max(errs) < 5e-2
+
+
 # --------------------------------------------------------------------------
 # coefficients and degree (Eq. 4, Eq. 6)
 # --------------------------------------------------------------------------
