@@ -50,6 +50,11 @@ WORKLOADS = {
     # The plain FP64 density matrix: 200 atoms x 4, 8 bohr cutoff, kT = 0.01, N_e = 400.
     "foe_fp64_800": dict(n_atoms=200, r_c=8.0, r_buf=4.0, kT=0.01, N_e=400.0, tol=1e-10, tol_S=1e-10,
                          precision="f64", n_mu=1),
+    # Batched: 64 independent systems of U{125..1500} atoms (seeds 0..63), 8 bohr
+    # cutoff, each with its own bounds, degree and mu; both passes one launch
+    # each, captured in CUDA graphs; autotuned tile shapes.
+    "foe_batched_64": dict(batched=True, n_sys=64, atoms_lo=125, atoms_hi=1500, r_c=8.0, r_buf=4.0, kT=0.01,
+                           tol=1e-7, tol_S=1e-10, precision="f32", n_mu=1),
 }
 DEFAULT_WORKLOAD = "foe_mixed_40k"
 
@@ -334,6 +339,103 @@ def run_cheb(args, rank: int, world: int, local: int):
         print(json.dumps(res), flush=True)
 
 
+def batched_sizes(cfg) -> list[int]:
+    rng = np.random.default_rng(0)
+    return [int(x) for x in rng.integers(cfg["atoms_lo"], cfg["atoms_hi"] + 1, cfg["n_sys"])]
+
+
+def run_batched(args, rank: int, world: int, local: int):
+    """The batched workload: one step = the density matrices of all systems of the batch."""
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_1704_00512_gb300 as cg
+    from paper_1704_00512_gb300 import batched
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = WORKLOADS[args.workload]
+    prec = cg.F32 if cfg["precision"] == "f32" else cg.F64
+    t0 = time.time()
+    sizes = batched_sizes(cfg)
+    systems = [synth.make_system(n, cfg["r_c"], seed=system_seed(rank) * 1000 + i) for i, n in enumerate(sizes)]
+    log(f"[rank {rank}] generated {len(systems)} systems, {sum(sizes)} atoms in {time.time() - t0:.1f}s")
+    bp = batched.BatchedProblem(systems, cfg["r_buf"], dev, precision=prec, log=log)
+    N_e = [2.0 * n for n in sizes]
+    kw = dict(tol=cfg["tol"], tol_S=cfg["tol_S"])
+    for i in range(args.warmup):
+        tw = time.time()
+        out = batched.foe_batched(bp, cfg["kT"], N_e, **kw)
+        log(f"[rank {rank}] warmup {i}: {time.time() - tw:.2f}s captured={out['captured']} "
+            f"n_terms {min(out['n_terms'])}..{max(out['n_terms'])} tiles={out['tiles']}")
+    clk = ClockSampler(local, enabled=not args.no_clocks)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = cg.launch_count()
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    passes = []
+    e0.record()
+    for _ in range(args.steps):
+        tm = {}
+        out = batched.foe_batched(bp, cfg["kT"], N_e, timings=tm, **kw)
+        passes.append(tm["pass1_ms"] + tm["pass2_ms"])
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = cg.launch_count() - l0
+    t_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    value = job_throughput(args.steps * len(systems), world, t_ms)
+    # end to end: H values from pinned host memory, F and the traces back
+    h_H = torch.from_numpy(np.concatenate([s.H for s in systems])).pin_memory()
+    h_F = torch.empty(tuple(out["F"].shape), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(args.e2e_steps):
+        bp.H.vals.copy_(h_H, non_blocking=True)
+        o = batched.foe_batched(bp, cfg["kT"], N_e, **kw)
+        h_F.copy_(o["F"], non_blocking=True)
+    f1.record()
+    torch.cuda.synchronize()
+    te_ms = max_over_ranks(f0.elapsed_time(f1), world, dev)
+    e2e_value = job_throughput(args.e2e_steps * len(systems), world, te_ms)
+    # roofline of the batched launches (FP32 ALU): block triples of every system x terms
+    triples = [count_triples(bp.PH[i].row_ptr.cpu().numpy(), bp.PH[i].col_idx.cpu().numpy(),
+                             bp.Pout[i].row_ptr.cpu().numpy(), bp.Pout[i].col_idx.cpu().numpy())
+               for i in range(len(systems))]
+    flops = sum(2.0 * 64.0 * t * 2 * (n - 2) for t, n in zip(triples, out["n_terms"]))
+    pass_s = statistics.mean(passes) / 1e3
+    tflops = flops / pass_s / 1e12
+    alu_peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    res = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": cfg["precision"], "data": "synthetic",
+        "config": {"workload": args.workload, "systems": len(systems), "atoms": sum(sizes),
+                   "atoms_range": [min(sizes), max(sizes)], "r_c": cfg["r_c"], "r_buf": cfg["r_buf"],
+                   "kT": cfg["kT"], "n_terms_range": [min(out["n_terms"]), max(out["n_terms"])],
+                   "blocks_P_out": bp.P_out.nnzb, "blocks_P_H": bp.P_H.nnzb, "tiles": out["tiles"],
+                   "graphs": "both passes captured and replayed", "l2": "inputs larger than L2 (no flush)"},
+        "roofline": {"bound": "alu", "achieved": round(tflops, 3), "peak": round(alu_peak, 3), "unit": "TFLOP/s",
+                     "frac": round(tflops / alu_peak, 4), "traffic": None, "kernel": "k_resident (batched)",
+                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"},
+        "pass_ms": round(statistics.mean(passes), 1),
+        "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": int(h_H.numel() * 8),
+                "d2h_bytes_per_step": int(h_F.numel() * 8)},
+        "gpu_launches": int(launches), "clocks": clocks,
+        "check": {"max_abs_trace_error": float(np.max(np.abs(out["trace_FS"] - np.array(N_e))))},
+    }
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
 # --------------------------------------------------------------------------
 # the CPU oracle: baseline leg and reference arm
 # --------------------------------------------------------------------------
@@ -369,11 +471,48 @@ def cpu_baseline(sysm, cfg, n_terms, n_S) -> dict:
                       f"{eq:.0f} step-equivalents per solve"}
 
 
+def run_reference_batched(args, cfg):
+    """Reference arm of the batched workload: the oracle's step time on the
+    median-size system, scaled per system by its blocks and step-equivalents."""
+    import synth
+    from oracle import ref
+    sizes = batched_sizes(cfg)
+    med = sorted(sizes)[len(sizes) // 2]
+    sysm = synth.make_system(med, cfg["r_c"], seed=0)
+    n_terms = ref.choose_degree(ref.Func(ref.KIND_FERMI, mu=0.0, kT=cfg["kT"]), -8.6, 8.6, cfg["tol"], 16384)
+    n_S = ref.choose_degree(ref.Func(ref.KIND_POWER, a=-0.5), 0.03, 3.1, cfg["tol_S"], 512, rel=True)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t_step, nnz_out = oracle_sample(sysm, cfg, 1)
+        if i >= args.warmup:
+            times.append(t_step)
+    eq = solve_step_equivalents(n_terms, n_S, nnz_out, sysm.nnzb)
+    # work per system ~ its P_out blocks: n_atoms x min(n_atoms, neighbours within r_c + r_buf)
+    rho = 200.0 / 18.0 ** 3
+    nb = lambda n: n * min(n, 1 + rho * 4.0 / 3.0 * np.pi * (cfg["r_c"] + cfg["r_buf"]) ** 3)
+    t_batch = statistics.mean(times) * eq * sum(nb(n) for n in sizes) / nb(med)
+    value = len(sizes) / t_batch
+    return value, t_batch, {"workload": args.workload, "systems": len(sizes), "atoms": sum(sizes),
+                            "sample_atoms": med, "n_terms": n_terms, "n_S": n_S}, (
+        f"per bench step one FP64 oracle recursion step of the median ({med}-atom) system, scaled by "
+        f"{eq:.0f} step-equivalents and by the batch's P_out blocks")
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
     import synth
     cfg = WORKLOADS[args.workload]
+    if cfg.get("batched"):
+        value, t_solve, conf, sample = run_reference_batched(args, cfg)
+        res = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": conf,
+               "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": sample},
+               "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(res), flush=True)
+        return
     sysm = synth.make_system(cfg["n_atoms"], cfg["r_c"], seed=0)
     # term counts of the solve come from the oracle's own degree rule on a
     # representative interval; the sample times one recursion step per bench step
@@ -416,6 +555,8 @@ def main():
     rank, world, local = rank_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif WORKLOADS[args.workload].get("batched"):
+        run_batched(args, rank, world, local)
     else:
         run_cheb(args, rank, world, local)
 

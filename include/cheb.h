@@ -287,6 +287,18 @@ int cheb_masked_product(const cheb_plan *plan, const cheb_bsr *L, const double *
  * not alias A.  Asynchronous. */
 int cheb_transpose(const cheb_plan *plan, const double *A, double *out, void *stream);
 
+/* Block-diagonal concatenation (setup of a batched expansion; not in the
+ * paper).  parts: host array of nsys BCSR descriptors (device pointers).
+ * out_row_ptr: device int64[sum of nbr + 1] = each part's row pointers shifted
+ * by the blocks of the parts before it; out_col_idx: device int32[sum of nnzb]
+ * = each part's column indices shifted by the rows of the parts before it;
+ * out_vals (device, may be NULL): the parts' values in order, elem_bytes (4 or
+ * 8) per element, 16 elements per block.  Asynchronous.  Errors:
+ * CHEB_ERR_INVALID for nsys < 1, NULL or inconsistent parts, more than
+ * INT32_MAX block rows. */
+int cheb_block_diag(int32_t nsys, const cheb_bsr *parts, int64_t *out_row_ptr, int32_t *out_col_idx,
+                    void *out_vals, int32_t elem_bytes, void *stream);
+
 /* Keep the blocks of A (FP64 on pattern PA) that lie in pattern P: out = device
  * double[P->nnzb*16]; blocks of P outside PA are written as zero.
  * Asynchronous. */

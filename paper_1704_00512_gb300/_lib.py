@@ -29,7 +29,7 @@ EXPORTS = [
     "cheb_plan_destroy", "cheb_plan_attach_operator", "cheb_plan_bind_operator", "cheb_scale", "cheb_bounds_workspace_size", "cheb_bounds",
     "cheb_coeffs_workspace_size", "cheb_coeffs", "cheb_expand_workspace_size", "cheb_expand",
     "cheb_expand_stepwise_workspace_size", "cheb_expand_stepwise", "cheb_plan_create_batched",
-    "cheb_plan_resident_info", "cheb_expand_batched", "cheb_lincomb", "cheb_mlp_param_count",
+    "cheb_plan_resident_info", "cheb_expand_batched", "cheb_block_diag", "cheb_lincomb", "cheb_mlp_param_count",
     "cheb_mlp_forward", "cheb_mlp_loss", "cheb_mlp_backward", "cheb_mlp_adam", "cheb_mlp_features",
     "cheb_masked_product", "cheb_transpose", "cheb_restrict", "cheb_trace_workspace_size", "cheb_trace",
     "cheb_penalty_trace", "cheb_mu_search", "cheb_mu_search_noalloc", "cheb_newton_schulz", "cheb_newton_schulz_isqrt",
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
         "cheb_plan_create_batched": ([P(CBsr), i32, i32, i32, P(i64), P(p), P(sz), p], i32),
         "cheb_plan_resident_info": ([p, P(i64), P(i32), P(i32)], i32),
         "cheb_expand_batched": ([p, P(CBsr), i32, p, p, p, i32, i32, P(p), p, p, p, i32, i32, p, sz, p], i32),
+        "cheb_block_diag": ([i32, P(CBsr), p, p, p, i32, p], i32),
         "cheb_lincomb": ([i32, P(dbl), P(p), i64, p, p], i32),
         "cheb_mlp_param_count": ([], i32),
         "cheb_mlp_forward": ([p, p, i32, p, p, p], i32),
@@ -275,14 +276,19 @@ def make_funcs(funcs) -> ctypes.Array:
 
 
 def coeffs(funcs, emin: float, emax: float, tol: float, n_max: int, rel: bool = False, device="cuda",
-           stream=None) -> tuple[int, torch.Tensor]:
-    """cheb_coeffs: returns (n, device tensor [n_f, n_max] with zeros beyond n)."""
+           stream=None, out: torch.Tensor | None = None) -> tuple[int, torch.Tensor]:
+    """cheb_coeffs: returns (n, device tensor [n_f, n_max] with zeros beyond n).
+
+    out: optional contiguous FP64 device tensor of n_f * n_max values to write into."""
     lib = load()
     nf = len(funcs)
     nb = ctypes.c_size_t(0)
     _check(lib.cheb_coeffs_workspace_size(nf, n_max, ctypes.byref(nb)))
     ws = _ws(nb.value, device)
-    out = torch.empty((nf, n_max), dtype=torch.float64, device=device)
+    if out is None:
+        out = torch.empty((nf, n_max), dtype=torch.float64, device=device)
+    elif out.numel() != nf * n_max or out.dtype != torch.float64:
+        raise ValueError("coeffs: out must hold n_f * n_max float64 values")
     n = ctypes.c_int32(0)
     _check(lib.cheb_coeffs(make_funcs(funcs), nf, emin, emax, tol, int(rel), n_max, ctypes.byref(n), _ptr(out),
                            ctypes.c_void_p(_aligned(ws)), nb.value, _stream(stream)))
@@ -368,6 +374,20 @@ def expand_batched(plan: BatchedPlan, Mt: Bsr, max_terms: int, n_terms: torch.Te
     return ws
 
 
+def block_diag(parts: list[Bsr], with_vals: bool = True, stream=None) -> Bsr:
+    """cheb_block_diag: the block-diagonal concatenation of parts (FP64 values if with_vals)."""
+    dev = parts[0].row_ptr.device
+    nbr = sum(p.nbr for p in parts)
+    nnzb = sum(p.nnzb for p in parts)
+    rp = torch.empty(nbr + 1, dtype=torch.int64, device=dev)
+    ci = torch.empty(max(nnzb, 1), dtype=torch.int32, device=dev)[:nnzb]
+    vals = torch.empty((nnzb, 4, 4), dtype=torch.float64, device=dev) if with_vals else None
+    arr = (CBsr * len(parts))(*[p.c() for p in parts])
+    _check(load().cheb_block_diag(len(parts), arr, _ptr(rp), ctypes.c_void_p(ci.data_ptr()), _ptr(vals), 8,
+                                  _stream(stream)))
+    return Bsr(rp, ci, vals)
+
+
 def masked_product(plan: Plan, L: Bsr, R: torch.Tensor, C: torch.Tensor, alpha: float = 1.0,
                    D: torch.Tensor | None = None, beta: float = 0.0, stream=None) -> torch.Tensor:
     cb = L.c()
@@ -389,13 +409,23 @@ def restrict(A: Bsr, P: Bsr, out: torch.Tensor | None = None, stream=None) -> to
     return out
 
 
-def trace(A: Bsr, B: Bsr, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """cheb_trace: device scalar sum over B's pattern of A_ij B_ij."""
+def _trace_ws_bytes(B: Bsr) -> int:
+    nb = ctypes.c_size_t(0)
+    cbb = B.c()
+    _check(load().cheb_trace_workspace_size(ctypes.byref(cbb), ctypes.byref(nb)))
+    return nb.value
+
+
+def trace(A: Bsr, B: Bsr, out: torch.Tensor | None = None, stream=None, ws: torch.Tensor | None = None) -> torch.Tensor:
+    """cheb_trace: device scalar sum over B's pattern of A_ij B_ij (ws: optional preallocated workspace)."""
     lib = load()
     ca, cbb = A.c(), B.c()
     nb = ctypes.c_size_t(0)
     _check(lib.cheb_trace_workspace_size(ctypes.byref(cbb), ctypes.byref(nb)))
-    ws = _ws(nb.value, A.vals.device)
+    if ws is None:
+        ws = _ws(nb.value, A.vals.device)
+    elif ws.numel() < nb.value + 256:
+        raise ValueError("trace: workspace too small")
     out = torch.empty(1, dtype=torch.float64, device=A.vals.device) if out is None else out
     _check(lib.cheb_trace(ctypes.byref(ca), ctypes.byref(cbb), _ptr(out), ctypes.c_void_p(_aligned(ws)), nb.value,
                           _stream(stream)))
@@ -412,10 +442,15 @@ def penalty_trace(moments: torch.Tensor, n_terms: int, alpha: float, stream=None
 
 def mu_search(gmoments: torch.Tensor, n_terms: int, emin: float, emax: float, kind: int, kT: float, N_e: float,
               tol_N: float, max_iter: int = 100, bracket: tuple[float, float] | None = None,
-              stream=None) -> torch.Tensor:
-    """cheb_mu_search: returns the 48-byte device result as a uint8 tensor."""
-    res = torch.zeros(48, dtype=torch.uint8, device=gmoments.device)
-    ws = _ws(8 * n_terms, gmoments.device)
+              stream=None, result: torch.Tensor | None = None, ws: torch.Tensor | None = None) -> torch.Tensor:
+    """cheb_mu_search: returns the 48-byte device result as a uint8 tensor.
+
+    result / ws: optional preallocated result (48 bytes) and workspace (>= 8*n_terms + 256 bytes)."""
+    res = torch.zeros(48, dtype=torch.uint8, device=gmoments.device) if result is None else result
+    if ws is None:
+        ws = _ws(8 * n_terms, gmoments.device)
+    elif ws.numel() < 8 * n_terms + 256:
+        raise ValueError("mu_search: workspace too small")
     br = None if bracket is None else (ctypes.c_double * 2)(*bracket)
     _check(load().cheb_mu_search(_ptr(gmoments), n_terms, emin, emax, kind, kT, N_e, tol_N, max_iter, br,
                                  _ptr(res), ctypes.c_void_p(_aligned(ws)), 8 * n_terms, _stream(stream)))
@@ -438,6 +473,12 @@ def mu_search_noalloc(gmoments: torch.Tensor, n_terms: int, emin: float, emax: f
     _check(load().cheb_mu_search_noalloc(_ptr(gmoments), n_terms, emin, emax, kind, kT, N_e, tol_N, max_iter, br,
                                          _ptr(res), _stream(stream)))
     return res
+
+
+def decode_mu_batch(res: torch.Tensor) -> list[dict]:
+    """Unpack a [n, 48] batch of mu-search results with one host copy."""
+    host = res.cpu()
+    return [decode_mu_result(host[i]) for i in range(host.shape[0])]
 
 
 def decode_mu_result(res: torch.Tensor) -> dict:

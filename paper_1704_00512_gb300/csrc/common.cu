@@ -202,3 +202,57 @@ extern "C" int cheb_lincomb(int32_t n, const double *weights, const double *cons
     k_lincomb<<<1216, 256, 0, as_stream(stream)>>>(c, n, len, out);
     return check_launch("k_lincomb");
 }
+
+// Block-diagonal concatenation of BCSR matrices (the input of a batched
+// expansion): row pointers shifted by the blocks before each part, column
+// indices by the rows before it, values copied in order.
+namespace cheb {
+__global__ void k_shift_i64(const int64_t *in, int64_t n, int64_t add, int64_t *out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i] + add;
+}
+__global__ void k_shift_i32(const int32_t *in, int64_t n, int32_t add, int32_t *out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i] + add;
+}
+}  // namespace cheb
+
+extern "C" int cheb_block_diag(int32_t nsys, const cheb_bsr *parts, int64_t *out_row_ptr, int32_t *out_col_idx,
+                               void *out_vals, int32_t elem_bytes, void *stream) {
+    if (nsys < 1 || !parts || !out_row_ptr || !out_col_idx)
+        return fail(CHEB_ERR_INVALID, "cheb_block_diag: bad arguments");
+    if (out_vals && elem_bytes != 4 && elem_bytes != 8)
+        return fail(CHEB_ERR_INVALID, "cheb_block_diag: elem_bytes must be 4 or 8");
+    int64_t rows = 0, blocks = 0;
+    for (int i = 0; i < nsys; ++i) {
+        const cheb_bsr &M = parts[i];
+        if (M.nbr < 1 || M.nnzb < 0 || !M.row_ptr || (M.nnzb > 0 && !M.col_idx) || (out_vals && M.nnzb > 0 && !M.vals))
+            return fail(CHEB_ERR_INVALID, "cheb_block_diag: part %d: bad sizes or pointers", i);
+        rows += M.nbr;
+        blocks += M.nnzb;
+    }
+    if (rows >= (int64_t)INT32_MAX) return fail(CHEB_ERR_INVALID, "cheb_block_diag: too many block rows");
+    cudaStream_t s = as_stream(stream);
+    int64_t r0 = 0, b0 = 0;
+    int launches = 0;
+    for (int i = 0; i < nsys; ++i) {
+        const cheb_bsr &M = parts[i];
+        k_shift_i64<<<(unsigned)((M.nbr + 255) / 256), 256, 0, s>>>(M.row_ptr, M.nbr, b0, out_row_ptr + r0);
+        ++launches;
+        if (M.nnzb > 0) {
+            k_shift_i32<<<(unsigned)((M.nnzb + 255) / 256), 256, 0, s>>>(M.col_idx, M.nnzb, (int32_t)r0,
+                                                                         out_col_idx + b0);
+            ++launches;
+            if (out_vals)
+                CHEB_CUDA(cudaMemcpyAsync(static_cast<char *>(out_vals) + b0 * BB * elem_bytes, M.vals,
+                                          (size_t)M.nnzb * BB * elem_bytes, cudaMemcpyDeviceToDevice, s));
+        }
+        r0 += M.nbr;
+        b0 += M.nnzb;
+    }
+    // the closing row pointer: the last part's end, shifted like its other rows
+    const cheb_bsr &L = parts[nsys - 1];
+    k_shift_i64<<<1, 1, 0, s>>>(L.row_ptr + L.nbr, 1, b0 - L.nnzb, out_row_ptr + rows);
+    ++launches;
+    return check_launch("cheb_block_diag", launches);
+}
