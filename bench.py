@@ -40,6 +40,12 @@ WORKLOADS = {
     # The mixed-precision density matrix: 10,000 atoms x 4, 10 bohr cutoff.
     "foe_mixed_40k": dict(n_atoms=10000, r_c=10.0, r_buf=4.0, kT=0.005, N_e=20000.0, tol=1e-7, tol_S=1e-10,
                           precision="f32", n_mu=4),
+    # The same solve in one pass: the learned mu proposal (weights trained by
+    # paper_1704_00512_gb300/train_mu.py) brackets mu*, 8 accumulators at
+    # Chebyshev nodes of the bracket, bisection on the same pass judges, a
+    # second pass only if mu* falls outside the bracket.
+    "foe_mixed_40k_learned": dict(n_atoms=10000, r_c=10.0, r_buf=4.0, kT=0.005, N_e=20000.0, tol=1e-7,
+                                  tol_S=1e-10, precision="f32", n_mu=8, form="learned", max_half_kT=0.5),
     # The same solve on 3,000 atoms (12,000 rows): profiling stand-in for the launch list.
     "foe_mixed_12k": dict(n_atoms=3000, r_c=10.0, r_buf=4.0, kT=0.005, N_e=6000.0, tol=1e-7, tol_S=1e-10,
                           precision="f32", n_mu=4),
@@ -213,11 +219,21 @@ def run_cheb(args, rank: int, world: int, local: int):
     sysm = synth.make_system(cfg["n_atoms"], cfg["r_c"], seed=system_seed(rank))
     log(f"[rank {rank}] generated {sysm.n_rows} rows, {sysm.nnzb} blocks in {time.time() - t0:.1f}s")
     pb = solve.problem_from_system(sysm, cfg["r_buf"], dev, prec)
-    kw = dict(kT=cfg["kT"], N_e=cfg["N_e"], tol=cfg["tol"], tol_S=cfg["tol_S"], n_mu=cfg["n_mu"])
+    learned_form = cfg.get("form") == "learned"
+    if learned_form:
+        from paper_1704_00512_gb300 import learned
+        prop = learned.load_proposal(dev)
+        kw = dict(kT=cfg["kT"], N_e=cfg["N_e"], tol=cfg["tol"], n_mu=cfg["n_mu"], max_half_kT=cfg["max_half_kT"])
 
-    def step(timings=None):
-        pb.build_patterns()
-        return solve.foe(pb, timings=timings, **kw)
+        def step(timings=None):
+            pb.build_patterns()
+            return learned.foe_learned(pb, prop, timings=timings, **kw)
+    else:
+        kw = dict(kT=cfg["kT"], N_e=cfg["N_e"], tol=cfg["tol"], tol_S=cfg["tol_S"], n_mu=cfg["n_mu"])
+
+        def step(timings=None):
+            pb.build_patterns()
+            return solve.foe(pb, timings=timings, **kw)
 
     for i in range(args.warmup):
         tw = time.time()
@@ -285,12 +301,21 @@ def run_cheb(args, rank: int, world: int, local: int):
     # ---- roofline of the dominant kernel (the fused recursion step)
     esz = 4 if prec == cg.F32 else 8
     steps_per_pass = n_terms - 2
-    b1 = step_bytes(nnz_out, nnz_H, esz, 0, True)
-    b2 = step_bytes(nnz_out, nnz_H, esz, cfg["n_mu"], False)
+    if learned_form:
+        # pass 1: n_mu accumulators + G; pass 2 (only on a miss): one accumulator
+        n_pass = out["passes"]
+        b1 = step_bytes(nnz_out, nnz_H, esz, cfg["n_mu"], True)
+        b2 = step_bytes(nnz_out, nnz_H, esz, 1, False) if n_pass == 2 else 0
+        if n_pass == 1:
+            p2 = 0.0
+    else:
+        n_pass = 2
+        b1 = step_bytes(nnz_out, nnz_H, esz, 0, True)
+        b2 = step_bytes(nnz_out, nnz_H, esz, cfg["n_mu"], False)
     flops = 2.0 * 64.0 * triples
     pass_s = (p1 + p2) / 1e3
     gbs = (b1 + b2) * steps_per_pass / pass_s / 1e9
-    tflops = 2 * flops * steps_per_pass / pass_s / 1e12
+    tflops = n_pass * flops * steps_per_pass / pass_s / 1e12
     hbm_peak, hbm_src = measured_hbm_peak()
     if prec == cg.F32:
         alu_peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
@@ -307,9 +332,9 @@ def run_cheb(args, rank: int, world: int, local: int):
         roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(hbm_frac, 4), "traffic": None, "peak_source": f"{hbm_src} copy bandwidth"}
     roof["kernel"] = "k_step<float,4,16>" if prec == cg.F32 else "k_step<double,2,8>"
-    roof["algorithmic_bytes_per_launch"] = int((b1 + b2) / 2)
+    roof["algorithmic_bytes_per_launch"] = int((b1 + b2) / n_pass)
     roof["algorithmic_flops_per_launch"] = flops
-    roof["avg_launch_ms"] = round((p1 + p2) / (2 * steps_per_pass), 5)
+    roof["avg_launch_ms"] = round((p1 + p2) / (n_pass * steps_per_pass), 5)
 
     res = {
         "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -329,7 +354,8 @@ def run_cheb(args, rank: int, world: int, local: int):
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clocks,
-        "check": {"trace_FS": float(out["trace_FS"].item()), "mu": out["mu"]},
+        "check": {"trace_FS": float(out["trace_FS"].item()), "mu": out["mu"], "passes": n_pass,
+                  **({"mu_hat": out["mu_hat"], "half_kT": out["half"] / cfg["kT"]} if learned_form else {})},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(sysm, cfg, n_terms, out["n_S"])

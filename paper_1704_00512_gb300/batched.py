@@ -147,14 +147,15 @@ def _pack_coeffs(funcs_per_sys, bounds, n_terms, device) -> tuple[torch.Tensor, 
     return buf, torch.as_tensor(off[:-1], dtype=torch.int64, device=device)
 
 
-def foe_batched(bp: BatchedProblem, kT: float, N_e: list[float], tol: float = 1e-7, tol_S: float = 1e-10,
-                kind: int = L.FERMI, lanczos_k: int = 40, n_max: int = 16384, max_iter: int = 100,
-                tol_N: list[float] | None = None, use_graphs: bool = True, timings: dict | None = None) -> dict:
-    """Density matrices of every system of the batch (see the module docstring)."""
-    tm = {} if timings is None else timings
+def prepare_batched(bp: BatchedProblem, kT, tol: float = 1e-7, tol_S: float = 1e-10, kind: int = L.FERMI,
+                    lanczos_k: int = 40, n_max: int = 16384) -> dict:
+    """Steps 2-3 of the module docstring: S^-1/2, H~', per-system bounds and degrees, G.
+
+    kT: one smearing for every system, or a list with one per system (it sets
+    each system's degree)."""
     dev = bp.device
-    t0 = time.perf_counter()
     nsys = bp.nsys
+    kTs = list(kT) if isinstance(kT, (list, tuple, np.ndarray)) else [kT] * nsys
     # --- S^-1/2 of every system: one batched FP64 power expansion
     bS = []
     for i in range(nsys):
@@ -186,12 +187,26 @@ def foe_batched(bp: BatchedProblem, kT: float, N_e: list[float], tol: float = 1e
         e0, e1, _ = L.bounds(Hi, lanczos_k)
         bH.append((e0, e1))
         L.scale(Hi, e0, e1, out=Hpt[bp.hoff[i]:bp.hoff[i + 1]])
-        nH.append(L.coeffs([{"kind": kind, "mu": 0.5 * (e0 + e1), "kT": kT}], e0, e1, tol, n_max, device=dev)[0])
+        nH.append(L.coeffs([{"kind": kind, "mu": 0.5 * (e0 + e1), "kT": kTs[i]}], e0, e1, tol, n_max,
+                           device=dev)[0])
     Hpt = bp.P_H.with_vals(Hpt)
     # trace functional G = transpose of P_out(A P_out(S A))
     L.masked_product(bp.plan64, bp.S, A, Y)
     L.masked_product(bp.plan64, bp.P_out.with_vals(A), Y, Z)
     G = L.transpose(bp.plan64, Z)
+    return {"A": A, "Hpt": Hpt, "G": G, "bounds_S": bS, "n_S": nS, "bounds_H": bH, "n_terms": nH}
+
+
+def foe_batched(bp: BatchedProblem, kT: float, N_e: list[float], tol: float = 1e-7, tol_S: float = 1e-10,
+                kind: int = L.FERMI, lanczos_k: int = 40, n_max: int = 16384, max_iter: int = 100,
+                tol_N: list[float] | None = None, use_graphs: bool = True, timings: dict | None = None) -> dict:
+    """Density matrices of every system of the batch (see the module docstring)."""
+    tm = {} if timings is None else timings
+    dev = bp.device
+    t0 = time.perf_counter()
+    nsys = bp.nsys
+    pr = prepare_batched(bp, kT, tol, tol_S, kind, lanczos_k, n_max)
+    A, Hpt, G, bS, nS, bH, nH = (pr[k] for k in ("A", "Hpt", "G", "bounds_S", "n_S", "bounds_H", "n_terms"))
     torch.cuda.synchronize(dev)
     tm["setup_s"] = time.perf_counter() - t0
 
@@ -300,3 +315,30 @@ def _fill_pass2_coeffs(st, kind, kT, mus, bH, nH, dev):
     for i, (mu, (e0, e1), n) in enumerate(zip(mus, bH, nH)):
         L.coeffs([{"kind": kind, "mu": mu, "kT": kT}], e0, e1, 0.0, int(n), device=dev,
                  out=st["c"][off[i]:off[i + 1]])
+
+
+def moment_pass_batched(bp: BatchedProblem, kT, N_e: list[float], n_moments: int = 32, tol: float = 1e-7,
+                        tol_S: float = 1e-10, kind: int = L.FERMI, max_iter: int = 100,
+                        tol_N: list[float] | None = None) -> dict:
+    """Pass 1 only, for every system: the first n_moments traces t_k = Tr T_k of
+    H~'_i, the trace functional moments g_k and each system's bisection result
+    (used to label training instances of the learned mu proposal)."""
+    dev = bp.device
+    nsys = bp.nsys
+    kTs = list(kT) if isinstance(kT, (list, tuple, np.ndarray)) else [kT] * nsys
+    pr = prepare_batched(bp, kTs, tol, tol_S, kind)
+    nH, bH = pr["n_terms"], pr["bounds_H"]
+    kmax = max(nH)
+    planX = bp.batched_plan(bp.precision, pr["Hpt"])
+    g = torch.zeros((nsys, kmax), dtype=torch.float64, device=dev)
+    t = torch.zeros((nsys, kmax), dtype=torch.float64, device=dev)
+    L.expand_batched(planX, pr["Hpt"], kmax, torch.as_tensor(nH, dtype=torch.int32, device=dev), None, None, 0,
+                     [], moments=t, G=pr["G"], gmoments=g, moment_stride=kmax, precision=bp.precision)
+    res = torch.zeros((nsys, 48), dtype=torch.uint8, device=dev)
+    tolN = [1e-6 * n for n in N_e] if tol_N is None else tol_N
+    for i in range(nsys):
+        L.mu_search(g[i], nH[i], bH[i][0], bH[i][1], kind, kTs[i], N_e[i], tolN[i], max_iter, result=res[i])
+    out = dict(pr)
+    out.update({"t": t[:, :n_moments].contiguous(), "g": g, "mu_result": L.decode_mu_batch(res)})
+    out["mu"] = [r["mu"] for r in out["mu_result"]]
+    return out

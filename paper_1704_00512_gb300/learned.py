@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
 
 import numpy as np
 import torch
@@ -27,6 +28,7 @@ from . import solve
 
 N_IN = 35
 N_MOM = 32
+N_PARAMS_EXPECTED = 35 * 128 + 128 + 128 * 128 + 128 + 2 * 128 + 2
 
 
 @dataclasses.dataclass
@@ -51,10 +53,10 @@ def prepare(pb: solve.Problem, tol_S: float = 1e-10, lanczos_k: int = 40):
     return A, Hpt, (e0, e1), G
 
 
-def moments32(pb: solve.Problem, Hpt: L.Bsr) -> torch.Tensor:
+def moments32(pb: solve.Problem, Hpt: L.Bsr, stepwise: bool = False) -> torch.Tensor:
     """t_k = Tr T_k for k < 32 (a 32-term expansion with no accumulators)."""
     t = torch.zeros(N_MOM, dtype=torch.float64, device=pb.device)
-    L.expand(pb.planX, Hpt, N_MOM, None, [], moments=t, precision=pb.precision)
+    L.expand(pb.planX, Hpt, N_MOM, None, [], moments=t, precision=pb.precision, stepwise=stepwise)
     return t
 
 
@@ -76,6 +78,25 @@ def label_instance(sysm, r_buf: float, kT: float, N_e: float, device, tol: float
     f = features(pb, t[:N_MOM].contiguous(), (e0, e1), N_e).cpu().numpy()
     sigma, tau = 2.0 / (e1 - e0), 0.5 * (e0 + e1)
     return Instance(f, sigma * (r["mu"] - tau), sigma * kT, kT, (e0, e1), r["mu"], n)
+
+
+def label_batch(systems, kTs, r_buf: float, device, tol: float = 1e-7, precision: int = L.F32):
+    """Features, scaled mu* and scale sigma*kT of many instances from one batched
+    moment pass (each instance half filled, N_e = rows/2)."""
+    from . import batched
+    bp = batched.BatchedProblem(systems, r_buf, device, precision=precision, tune=False)
+    N_e = [2.0 * s.n_atoms for s in systems]
+    mp = batched.moment_pass_batched(bp, list(kTs), N_e, n_moments=N_MOM, tol=tol)
+    X = torch.empty((len(systems), N_IN), dtype=torch.float32, device=bp.device)
+    xstar, scale = np.zeros(len(systems)), np.zeros(len(systems))
+    for i, s in enumerate(systems):
+        e0, e1 = mp["bounds_H"][i]
+        L.mlp_features(mp["t"][i], s.n_rows, e0, e1, N_e[i], X[i])
+        sigma, tau = 2.0 / (e1 - e0), 0.5 * (e0 + e1)
+        xstar[i] = sigma * (mp["mu"][i] - tau)
+        scale[i] = sigma * kTs[i]
+    conv = all(r["converged"] for r in mp["mu_result"])
+    return X.cpu().numpy(), xstar, scale, {"mu": mp["mu"], "n_terms": mp["n_terms"], "converged": conv}
 
 
 class Proposal:
@@ -129,6 +150,20 @@ class Proposal:
         return hist
 
 
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "mu_proposal.npz")
+
+
+def load_proposal(device, path: str = WEIGHTS) -> Proposal:
+    """The trained proposal written by train_mu.py."""
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} missing: train it with python -m paper_1704_00512_gb300.train_mu")
+    with np.load(path) as d:
+        theta = d["theta"]
+    if theta.shape != (N_PARAMS_EXPECTED,):
+        raise ValueError(f"{path}: {theta.shape[0]} parameters, expected {N_PARAMS_EXPECTED}")
+    return Proposal(theta, device)
+
+
 def chebyshev_nodes(center: float, half: float, n: int) -> list[float]:
     return [center + half * math.cos(math.pi * (i + 0.5) / n) for i in range(n)]
 
@@ -144,38 +179,53 @@ def lagrange_weights(nodes: list[float], x: float) -> list[float]:
     return w
 
 
-def foe_learned(pb: solve.Problem, prop: Proposal, kT: float, N_e: float, tol: float = 1e-7, n_mu: int = 4,
+def foe_learned(pb: solve.Problem, prop: Proposal, kT: float, N_e: float, tol: float = 1e-7, n_mu: int = 8,
                 min_half_kT: float = 0.05, max_half_kT: float = 1.0, tol_N: float | None = None,
-                prepared=None) -> dict:
-    """One-expansion FOE with the learned bracket; bisection judges, fallback on a miss."""
+                prepared=None, bracket: tuple[float, float] | None = None, stepwise: bool = True,
+                timings: dict | None = None) -> dict:
+    """One-expansion FOE with the learned bracket; bisection judges, fallback on a miss.
+
+    With n_mu = 8 Chebyshev nodes the interpolation error of the Fermi function
+    in mu stays below 4e-7 for a half-width of one kT and below 2e-9 for half a
+    kT.  bracket: (mu_hat, half) to use instead of the network's (tests)."""
+    tm = {} if timings is None else timings
     A, Hpt, (e0, e1), G = prepare(pb) if prepared is None else prepared
     sigma, tau = 2.0 / (e1 - e0), 0.5 * (e0 + e1)
-    t32 = moments32(pb, Hpt)
-    X = features(pb, t32, (e0, e1), N_e).view(1, N_IN)
-    o = prop.forward(X).cpu().numpy()[0]
-    mu_hat = float(o[0]) / sigma + tau
-    half = math.exp(float(o[1])) / sigma
-    half = min(max(half, min_half_kT * kT), max_half_kT * kT)
+    if bracket is None:
+        t32 = moments32(pb, Hpt, stepwise=stepwise)
+        X = features(pb, t32, (e0, e1), N_e).view(1, N_IN)
+        o = prop.forward(X).cpu().numpy()[0]
+        mu_hat = float(o[0]) / sigma + tau
+        half = math.exp(float(o[1])) / sigma
+        half = min(max(half, min_half_kT * kT), max_half_kT * kT)
+    else:
+        mu_hat, half = bracket
     mus = chebyshev_nodes(mu_hat, half, n_mu)
     # same term count as the plain solve (degree chosen at the interval centre)
     n, _ = L.coeffs([{"kind": L.FERMI, "mu": tau, "kT": kT}], e0, e1, tol, 16384, device=pb.device)
     _, c = L.coeffs([{"kind": L.FERMI, "mu": m, "kT": kT} for m in mus], e0, e1, 0.0, n, device=pb.device)
     accs = [pb.zeros_out() for _ in mus]
     g = torch.zeros(n, dtype=torch.float64, device=pb.device)
-    ws = L.expand(pb.planX, Hpt, n, c, accs, G=G, gmoments=g, precision=pb.precision)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    ws = L.expand(pb.planX, Hpt, n, c, accs, G=G, gmoments=g, precision=pb.precision, stepwise=stepwise)
+    ev[1].record()
     if tol_N is None:
         tol_N = 1e-6 * N_e
     r = L.decode_mu_result(L.mu_search(g, n, e0, e1, L.FERMI, kT, N_e, tol_N))
     mu = r["mu"]
     passes = 1
     p = pb.zeros_out()
+    ev[2].record()
     if abs(mu - mu_hat) <= half:
         L.lincomb(lagrange_weights(mus, mu), accs, p)
     else:
         _, c2 = L.coeffs([{"kind": L.FERMI, "mu": mu, "kT": kT}], e0, e1, 0.0, n, device=pb.device)
-        L.expand(pb.planX, Hpt, n, c2, [p], precision=pb.precision, ws=ws)
+        L.expand(pb.planX, Hpt, n, c2, [p], precision=pb.precision, ws=ws, stepwise=stepwise)
         passes = 2
+    ev[3].record()
     F = solve.postprocess(pb, A, p)
     trFS = L.trace(pb.P_out.with_vals(F), pb.S)
+    tm["events"] = ev
     return {"F": F, "p": p, "mu": mu, "mu_hat": mu_hat, "half": half, "passes": passes, "n_terms": n,
-            "mu_result": r, "trace_FS": trFS, "bounds_H": (e0, e1)}
+            "mu_result": r, "trace_FS": trFS, "bounds_H": (e0, e1), "n_mu": n_mu}
