@@ -45,7 +45,7 @@ WORKLOADS = {
     # Chebyshev nodes of the bracket, bisection on the same pass judges, a
     # second pass only if mu* falls outside the bracket.
     "foe_mixed_40k_learned": dict(n_atoms=10000, r_c=10.0, r_buf=4.0, kT=0.005, N_e=20000.0, tol=1e-7,
-                                  tol_S=1e-10, precision="f32", n_mu=8, form="learned", max_half_kT=0.5),
+                                  tol_S=1e-10, precision="f32", n_mu=8, form="learned", max_half_kT=1.0),
     # The same solve on 3,000 atoms (12,000 rows): profiling stand-in for the launch list.
     "foe_mixed_12k": dict(n_atoms=3000, r_c=10.0, r_buf=4.0, kT=0.005, N_e=6000.0, tol=1e-7, tol_S=1e-10,
                           precision="f32", n_mu=4),

@@ -200,6 +200,43 @@ def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FE
             "n_S": pw["n_terms"], "trace_FS": trFS}
 
 
+def selected_eigenvalues(pb: Problem, kT: float, intervals=(), levels=(), tol: float = 1e-9, n_max: int = 16384,
+                         lanczos_k: int = 40, tol_S: float = 1e-10, bounds_S=None, n_S=None, bounds_H=None,
+                         tol_N: float = 1e-10) -> dict:
+    """Sec. "Extraction of selected eigenvalues": eigenvalue counts and levels.
+
+    For each interval (lo, hi) the projector Q = f_FD(H; hi) - f_FD(H; lo) is
+    accumulated (one FP64 accumulator each, all in one recursion) and post-
+    processed like F; Tr(Q S) counts the eigenvalues in (lo, hi).  For each
+    level N the bisection on the trace functional of the same recursion finds
+    the mu with Tr(F(mu) S) = N - 1/2, which lies at the N-th eigenvalue when
+    kT is small against the gaps around it."""
+    pw = powers(pb, exponents=(-0.5,), tol=tol_S, bounds_S=bounds_S, n_terms=n_S, precision=L.F64)
+    A = pw["acc"][0]
+    Hp = orthogonalise(pb, A)
+    e0, e1 = L.bounds(Hp, lanczos_k)[:2] if bounds_H is None else bounds_H
+    Hpt = Hp.with_vals(L.scale(Hp, e0, e1))
+    G = trace_functional(pb, A)
+    funcs = [{"kind": L.INTERVAL, "lo": lo, "hi": hi, "kT": kT} for lo, hi in intervals]
+    fdeg = funcs + [{"kind": L.FERMI, "mu": 0.5 * (e0 + e1), "kT": kT}]
+    n, _ = L.coeffs(fdeg, e0, e1, tol, n_max, device=pb.device)
+    c = L.coeffs(funcs, e0, e1, 0.0, n, device=pb.device)[1] if funcs else None
+    accs = [pb.zeros_out() for _ in funcs]
+    g = torch.zeros(n, dtype=torch.float64, device=pb.device)
+    L.expand(pb.plan64, Hpt, n, c, accs, G=G, gmoments=g, precision=L.F64, stepwise=True)
+    counts, Qs = [], []
+    for Q in accs:
+        Qp = postprocess(pb, A, Q)
+        Qs.append(Qp)
+        counts.append(float(L.trace(pb.P_out.with_vals(Qp), pb.S).item()))
+    eigs = []
+    for N in levels:
+        r = L.decode_mu_result(L.mu_search(g, n, e0, e1, L.FERMI, kT, N - 0.5, tol_N, 128))
+        eigs.append(r["mu"])
+    return {"counts": counts, "Q": Qs, "eigenvalues": eigs, "n_terms": n, "bounds_H": (e0, e1),
+            "bounds_S": pw["bounds"], "n_S": pw["n_terms"], "gmoments": g}
+
+
 def foe_solve(sysm, r_buf: float, kT: float, N_e: float, tol: float = 1e-10, precision: int = L.F64,
               device="cuda", **kw) -> dict:
     """foe() on a synthetic system, with host copies of the main results."""

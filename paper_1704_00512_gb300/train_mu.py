@@ -50,7 +50,7 @@ def make_instances(n_batches: int, per_batch: int, atoms_lo: int, atoms_hi: int,
 
 
 def evaluate(prop: learned.Proposal, X: np.ndarray, xstar: np.ndarray, scale: np.ndarray,
-             min_half_kT: float = 0.05, max_half_kT: float = 0.5) -> dict:
+             min_half_kT: float = 0.05, max_half_kT: float = 1.0) -> dict:
     """Distance of the proposal from mu* in kT and the fraction of (clamped) brackets holding mu*."""
     out = prop.forward(torch.as_tensor(X, dtype=torch.float32, device=prop.device).contiguous()).cpu().numpy()
     d = np.abs(out[:, 0] - xstar) / scale

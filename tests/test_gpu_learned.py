@@ -119,7 +119,7 @@ def test_fallback_when_the_bracket_misses():
 
 def test_one_pass_form_at_the_bench_degree_within_target_of_fp64():
     # The one-pass form the bench uses (FP32 recursion, 8 mu nodes over a
-    # bracket of half-width 0.5 kT holding mu*, Lagrange interpolation, FP64
+    # bracket of half-width up to 1 kT holding mu*, Lagrange interpolation, FP64
     # accumulators) against the plain two-pass FP64 solve, at the bench's kT
     # and fit tolerance (~9e3 terms) on a 2,000-row system.
     s = synth.make_system(500, 10.0, 19)
@@ -127,12 +127,15 @@ def test_one_pass_form_at_the_bench_degree_within_target_of_fp64():
     ref64 = solve.foe_solve(s, 4.0, kT=kT, N_e=N_e, tol=1e-7, tol_S=1e-10, device=DEV)
     pb = solve.problem_from_system(s, 4.0, DEV, cg.F32)
     prop = learned.Proposal(np.zeros(omlp.N_PARAMS), DEV)  # unused: the bracket is given
-    out = learned.foe_learned(pb, prop, kT, N_e, tol=1e-7, n_mu=8, bracket=(ref64["mu"] + 0.3 * kT, 0.5 * kT))
-    F = out["F"].cpu().numpy()
-    err = np.linalg.norm(F - ref64["F_host"]) / np.linalg.norm(ref64["F_host"])
-    print(f"one-pass FP32 form: n_terms={out['n_terms']} relF vs FP64 plain = {err:.3e}, "
-          f"|mu - mu64| = {abs(out['mu'] - ref64['mu']):.2e}")
-    assert out["passes"] == 1
-    assert out["n_terms"] >= 7000
-    assert err < 1e-6
-    assert abs(out["trace_FS"].item() - N_e) < 1e-6 * N_e
+    prep = learned.prepare(pb)
+    for half_kT in (0.5, 1.0):
+        out = learned.foe_learned(pb, prop, kT, N_e, tol=1e-7, n_mu=8, prepared=prep,
+                                  bracket=(ref64["mu"] + 0.6 * half_kT * kT, half_kT * kT))
+        F = out["F"].cpu().numpy()
+        err = np.linalg.norm(F - ref64["F_host"]) / np.linalg.norm(ref64["F_host"])
+        print(f"one-pass FP32 form, half-width {half_kT} kT: n_terms={out['n_terms']} relF vs FP64 plain = "
+              f"{err:.3e}, |mu - mu64| = {abs(out['mu'] - ref64['mu']):.2e}")
+        assert out["passes"] == 1
+        assert out["n_terms"] >= 7000
+        assert err < 1e-6
+        assert abs(out["trace_FS"].item() - N_e) < 1e-6 * N_e

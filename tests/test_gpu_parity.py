@@ -573,3 +573,37 @@ def test_masked_product_row_lists(n_atoms, r_c, r_buf):
         want2 = ref.masked_product(ref.Bsr(P_out.row_ptr, P_out.col_idx, dO.vals.cpu().numpy()),
                                    P_out.with_vals(R.cpu().numpy()), P_out.row_ptr, P_out.col_idx)
         assert relF(C2.cpu().numpy(), want2) < 1e-13
+
+
+def test_selected_eigenvalues_counts_and_levels():
+    # Sec. "Extraction of selected eigenvalues" on a 40-row system whose
+    # patterns are dense: the interval projector counts the generalised
+    # eigenvalues in (lo, hi), the bisection to N - 1/2 lands on eps_N, and the
+    # GPU sequence matches the oracle's step by step.
+    import scipy.linalg as sla
+    s = synth.make_system(10, 30.0, 13)
+    S, H, P_out = pipelines.system_mats(s, 4.0)
+    eps = sla.eigh(H.dense(), S.dense(), eigvals_only=True)
+    kT = 0.01
+    gaps = np.diff(eps)
+    i = int(np.argmax(gaps[: len(gaps) // 2]))
+    j = len(gaps) // 2 + int(np.argmax(gaps[len(gaps) // 2:]))
+    lo, hi = 0.5 * (eps[i] + eps[i + 1]), 0.5 * (eps[j] + eps[j + 1])
+    N = 7
+    pb = solve.problem_from_system(s, 4.0, DEV, cg.F64)
+    out = solve.selected_eigenvalues(pb, kT, intervals=[(lo, hi)], levels=[N], tol=1e-9)
+    want = int(np.sum((eps > lo) & (eps < hi)))
+    assert abs(out["counts"][0] - want) < 1e-4, (out["counts"], want)
+    assert abs(out["eigenvalues"][0] - eps[N - 1]) < 3 * kT
+    # the oracle's steps with the same bounds and degrees
+    e0, e1 = out["bounds_H"]
+    A = pipelines.powers(S, P_out, (-0.5,), out["bounds_S"], out["n_S"])["acc"][0]
+    Hp = ref.orthogonalise(H, A, P_out)
+    G = ref.trace_functional_matrix(A, S, P_out)
+    c = ref.cheb_coeffs(ref.Func(ref.KIND_INTERVAL, kT=kT, lo=lo, hi=hi), out["n_terms"], e0, e1)
+    ex = ref.chebyshev_expand(ref.scale(Hp, e0, e1), P_out, c[None], G=G)
+    count = ref.trace_product(ref.postprocess(ex.acc[0], A, P_out), S)
+    assert abs(out["counts"][0] - count) < 1e-9 * max(1.0, abs(count))
+    assert relF(out["gmoments"].cpu().numpy(), ex.g) < 1e-10
+    r = ref.mu_bisect(ex.g, ref.KIND_FERMI, kT, e0, e1, N - 0.5, 1e-10, 128)
+    assert abs(out["eigenvalues"][0] - r.mu) < 1e-10
