@@ -135,7 +135,9 @@ class BatchedProblem:
         if precision not in self.tiles:
             self.tiles[precision] = (autotune_tile(self.P_out, self.starts, precision, Mt, log=self.log)
                                      if self.tune else -1)
-        return L.BatchedPlan(self.P_out, self.starts, precision, self.tiles[precision])
+        plan = L.BatchedPlan(self.P_out, self.starts, precision, self.tiles[precision])
+        # every batched expansion here runs on an operator with the pattern of P_H
+        return plan.attach_operator(self.P_H)
 
 
 def _pack_coeffs(funcs_per_sys, bounds, n_terms, device) -> tuple[torch.Tensor, torch.Tensor]:

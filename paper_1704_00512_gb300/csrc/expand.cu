@@ -618,9 +618,9 @@ StepArgs<T> base_args(const cheb_plan *plan, const cheb_bsr *L, const T *Lv) {
     a.Lci = L->col_idx;
     a.Lv = Lv;
     if (plan->op_bound && plan->op_rp == L->row_ptr && plan->op_ci == L->col_idx) {
-        a.lrow_base = plan->d_lrow_base;
-        a.lrow_ptr = plan->d_lrow_ptr;
-        a.lent = plan->d_lent;
+        a.lrow_base = plan->lists.d_base;
+        a.lrow_ptr = plan->lists.d_ptr;
+        a.lent = plan->lists.d_ent;
     }
     return a;
 }

@@ -277,17 +277,18 @@ extern "C" int cheb_plan_destroy(cheb_plan *plan) {
     return CHEB_OK;
 }
 
-// Panels [p0, p1) of the operator row lists: with count_only, the number of
-// list entries of each panel; otherwise the row pointers and entries, written
-// at the panel offsets the counts gave.
-static void build_row_lists(const cheb_plan *plan, const std::vector<int64_t> &rp, const std::vector<int32_t> &ci,
-                            const std::vector<int64_t> &lrp, const std::vector<int32_t> &lci, int64_t p0, int64_t p1,
-                            bool count_only, std::vector<int64_t> &cnt, std::vector<int64_t> &nrow,
-                            const std::vector<int64_t> &ent_off, std::vector<int32_t> &lrow_ptr,
-                            std::vector<int64_t> &lrow_base, std::vector<uint32_t> &lent) {
-    std::vector<int32_t> stamp(plan->nbr, -1), slot_of(plan->nbr, -1), uni;
+// Panels [p0, p1) of a panel set's operator row lists: with count_only, the
+// number of list entries of each panel; otherwise the row pointers and
+// entries, written at the panel offsets the counts gave.
+static void build_row_lists(int64_t nbr, const std::vector<int32_t> &panels, const std::vector<int64_t> &rp,
+                            const std::vector<int32_t> &ci, const std::vector<int64_t> &lrp,
+                            const std::vector<int32_t> &lci, int64_t p0, int64_t p1, bool count_only,
+                            std::vector<int64_t> &cnt, std::vector<int64_t> &nrow, const std::vector<int64_t> &ent_off,
+                            std::vector<int32_t> &lrow_ptr, std::vector<int64_t> &lrow_base,
+                            std::vector<uint32_t> &lent) {
+    std::vector<int32_t> stamp(nbr, -1), slot_of(nbr, -1), uni;
     for (int64_t p = p0; p < p1; ++p) {
-        const int32_t j0 = plan->h_panels[2 * p], nc = plan->h_panels[2 * p + 1];
+        const int32_t j0 = panels[2 * p], nc = panels[2 * p + 1];
         uni.clear();
         for (int32_t q = 0; q < nc; ++q)
             for (int64_t e = rp[j0 + q]; e < rp[j0 + q + 1]; ++e)
@@ -316,6 +317,44 @@ static void build_row_lists(const cheb_plan *plan, const std::vector<int64_t> &r
     }
 }
 
+// The row lists of one panel set (np panels), built on host threads.
+static int make_row_lists(int64_t nbr, const std::vector<int32_t> &panels, int64_t np, const std::vector<int64_t> &rp,
+                          const std::vector<int32_t> &ci, const std::vector<int64_t> &lrp,
+                          const std::vector<int32_t> &lci, RowLists &out) {
+    std::vector<int64_t> cnt(np), nrow(np), ent_off(np + 1), lrow_base(np + 1);
+    std::vector<int32_t> lrow_ptr;
+    std::vector<uint32_t> lent;
+    const int nth = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)std::thread::hardware_concurrency(), 16, np}));
+    auto run = [&](bool count_only) {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nth; ++t) {
+            const int64_t p0 = np * t / nth, p1 = np * (t + 1) / nth;
+            th.emplace_back([&, p0, p1] {
+                build_row_lists(nbr, panels, rp, ci, lrp, lci, p0, p1, count_only, cnt, nrow, ent_off, lrow_ptr,
+                                lrow_base, lent);
+            });
+        }
+        for (auto &x : th) x.join();
+    };
+    run(true);
+    ent_off[0] = lrow_base[0] = 0;
+    for (int64_t p = 0; p < np; ++p) {
+        ent_off[p + 1] = ent_off[p] + cnt[p];
+        lrow_base[p + 1] = lrow_base[p] + nrow[p];
+    }
+    if (ent_off[np] >= (int64_t)INT32_MAX)
+        return fail(CHEB_ERR_NOSPACE, "cheb_plan_attach_operator: %lld list entries exceed the int32 offsets",
+                    (long long)ent_off[np]);
+    lrow_ptr.resize(lrow_base[np]);
+    lent.resize(ent_off[np]);
+    run(false);
+    lrow_base.resize(np);
+    out.h_base.swap(lrow_base);
+    out.h_ptr.swap(lrow_ptr);
+    out.h_ent.swap(lent);
+    return CHEB_OK;
+}
+
 extern "C" int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, size_t *op_ws_bytes, void *stream) {
     if (!plan || !L || !op_ws_bytes || !L->row_ptr || !L->col_idx || L->nbr != plan->nbr)
         return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: bad arguments");
@@ -339,46 +378,31 @@ extern "C" int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, siz
             if (lci[a] < 0 || lci[a] >= nbr)
                 return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: column out of range in row %lld", (long long)I);
     }
-    const int64_t np = plan->n_panels;
-    std::vector<int64_t> cnt(np), nrow(np), ent_off(np + 1), lrow_base(np + 1);
-    std::vector<int32_t> lrow_ptr;
-    std::vector<uint32_t> lent;
-    const int nth = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)std::thread::hardware_concurrency(), 16, np}));
-    auto run = [&](bool count_only) {
-        std::vector<std::thread> th;
-        for (int t = 0; t < nth; ++t) {
-            const int64_t p0 = np * t / nth, p1 = np * (t + 1) / nth;
-            th.emplace_back([&, p0, p1] {
-                build_row_lists(plan, rp, ci, lrp, lci, p0, p1, count_only, cnt, nrow, ent_off, lrow_ptr, lrow_base,
-                                lent);
-            });
-        }
-        for (auto &x : th) x.join();
-    };
-    run(true);
-    ent_off[0] = lrow_base[0] = 0;
-    for (int64_t p = 0; p < np; ++p) {
-        ent_off[p + 1] = ent_off[p] + cnt[p];
-        lrow_base[p + 1] = lrow_base[p] + nrow[p];
-    }
-    if (ent_off[np] >= (int64_t)INT32_MAX)
-        return fail(CHEB_ERR_NOSPACE, "cheb_plan_attach_operator: %lld list entries exceed the int32 offsets",
-                    (long long)ent_off[np]);
-    lrow_ptr.resize(lrow_base[np]);
-    lent.resize(ent_off[np]);
-    run(false);
-    lrow_base.resize(np);
+    RowLists lists, rlists;
+    CHEB_TRY(make_row_lists(nbr, plan->h_panels, plan->n_panels, rp, ci, lrp, lci, lists));
+    if (plan->n_rpanels > 0)
+        CHEB_TRY(make_row_lists(nbr, plan->h_rpanels, plan->n_rpanels, rp, ci, lrp, lci, rlists));
     plan->op_rp = L->row_ptr;
     plan->op_ci = L->col_idx;
-    plan->n_list_rows = (int64_t)lrow_ptr.size();
-    plan->n_entries = (int64_t)lent.size();
-    plan->h_lrow_base.swap(lrow_base);
-    plan->h_lrow_ptr.swap(lrow_ptr);
-    plan->h_lent.swap(lent);
-    plan->op_ws_bytes = align_up(plan->h_lrow_base.size() * 8) + align_up(plan->h_lrow_ptr.size() * 4) +
-                        align_up(std::max<size_t>(plan->h_lent.size(), 1) * 4);
+    plan->lists = std::move(lists);
+    plan->rlists = std::move(rlists);
+    plan->op_ws_bytes = plan->lists.bytes() + plan->rlists.bytes();
     plan->op_bound = false;
     *op_ws_bytes = plan->op_ws_bytes;
+    return CHEB_OK;
+}
+
+// Device copies of one panel set's lists, carved from the operator workspace.
+static int bind_row_lists(RowLists &l, Carve &cv, cudaStream_t s) {
+    if (l.h_base.empty()) return CHEB_OK;
+    l.d_base = cv.take<int64_t>(l.h_base.size());
+    l.d_ptr = cv.take<int32_t>(l.h_ptr.size());
+    l.d_ent = cv.take<uint32_t>(std::max<size_t>(l.h_ent.size(), 1));
+    if (!cv.fits()) return fail(CHEB_ERR_NOSPACE, "cheb_plan_bind_operator: workspace too small");
+    CHEB_CUDA(cudaMemcpyAsync(l.d_base, l.h_base.data(), l.h_base.size() * 8, cudaMemcpyHostToDevice, s));
+    CHEB_CUDA(cudaMemcpyAsync(l.d_ptr, l.h_ptr.data(), l.h_ptr.size() * 4, cudaMemcpyHostToDevice, s));
+    if (!l.h_ent.empty())
+        CHEB_CUDA(cudaMemcpyAsync(l.d_ent, l.h_ent.data(), l.h_ent.size() * 4, cudaMemcpyHostToDevice, s));
     return CHEB_OK;
 }
 
@@ -388,21 +412,15 @@ extern "C" int cheb_plan_bind_operator(cheb_plan *plan, void *ws, size_t ws_byte
         return fail(CHEB_ERR_NOSPACE, "cheb_plan_bind_operator: workspace %zu < %zu or misaligned", ws_bytes,
                     plan->op_ws_bytes);
     Carve cv(ws, ws_bytes);
-    plan->d_lrow_base = cv.take<int64_t>(plan->h_lrow_base.size());
-    plan->d_lrow_ptr = cv.take<int32_t>(plan->h_lrow_ptr.size());
-    plan->d_lent = cv.take<uint32_t>(std::max<size_t>(plan->h_lent.size(), 1));
     cudaStream_t s = as_stream(stream);
-    CHEB_CUDA(cudaMemcpyAsync(plan->d_lrow_base, plan->h_lrow_base.data(), plan->h_lrow_base.size() * 8,
-                              cudaMemcpyHostToDevice, s));
-    CHEB_CUDA(cudaMemcpyAsync(plan->d_lrow_ptr, plan->h_lrow_ptr.data(), plan->h_lrow_ptr.size() * 4,
-                              cudaMemcpyHostToDevice, s));
-    if (!plan->h_lent.empty())
-        CHEB_CUDA(cudaMemcpyAsync(plan->d_lent, plan->h_lent.data(), plan->h_lent.size() * 4, cudaMemcpyHostToDevice,
-                                  s));
+    CHEB_TRY(bind_row_lists(plan->lists, cv, s));
+    CHEB_TRY(bind_row_lists(plan->rlists, cv, s));
     CHEB_CUDA(cudaStreamSynchronize(s));
     // the device copies are the only ones needed from here on
-    std::vector<int32_t>().swap(plan->h_lrow_ptr);
-    std::vector<uint32_t>().swap(plan->h_lent);
+    for (RowLists *l : {&plan->lists, &plan->rlists}) {
+        std::vector<int32_t>().swap(l->h_ptr);
+        std::vector<uint32_t>().swap(l->h_ent);
+    }
     plan->op_bound = true;
     return CHEB_OK;
 }

@@ -1,12 +1,28 @@
 // The plan object: transposition map and column panels of a symmetric output pattern.
 #pragma once
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
 
 // Largest dynamic shared memory a block may use on sm_100/sm_103 (227 KB).
 #define CHEB_MAX_DYN_SMEM 232448
+
+// Operator row lists of one panel set (see cheb_plan).
+struct RowLists {
+    std::vector<int64_t> h_base;  // [panels] first row pointer of each panel
+    std::vector<int32_t> h_ptr;   // [sum of (union + 1) over panels] entry offsets
+    std::vector<uint32_t> h_ent;  // entries
+    int64_t *d_base = nullptr;
+    int32_t *d_ptr = nullptr;
+    uint32_t *d_ent = nullptr;
+    size_t bytes() const {
+        return h_base.empty() ? 0
+                              : ::cheb::align_up(h_base.size() * 8) + ::cheb::align_up(h_ptr.size() * 4) +
+                                    ::cheb::align_up(std::max<size_t>(h_ent.size(), 1) * 4);
+    }
+};
 
 struct cheb_plan {
     int64_t nbr = 0;
@@ -42,22 +58,16 @@ struct cheb_plan {
     int32_t *d_rpanel_sys = nullptr;
     int32_t *d_sys_rpanel = nullptr;
     size_t ws_bytes = 0;
-    // Operator row lists (cheb_plan_attach_operator): for every step panel and
-    // each of its union rows (ascending block row), the operator row's blocks
-    // whose column lies in the union, as (offset of the block in the operator
-    // row << 16 | union slot of the column).  Valid for the operator pattern
-    // (op_rp, op_ci) only.
+    // Operator row lists (cheb_plan_attach_operator): for every panel and each
+    // of its union rows (ascending block row), the operator row's blocks whose
+    // column lies in the union, as (offset of the block in the operator row
+    // << 16 | union slot of the column).  One set for the per-step panels, one
+    // for the resident panels.  Valid for the operator pattern (op_rp, op_ci).
     const int64_t *op_rp = nullptr;
     const int32_t *op_ci = nullptr;
-    int64_t n_list_rows = 0, n_entries = 0;
-    std::vector<int64_t> h_lrow_base;  // [n_panels] first row pointer of each panel
-    std::vector<int32_t> h_lrow_ptr;   // [sum of (union + 1) over panels] entry offsets
-    std::vector<uint32_t> h_lent;      // [n_entries]
+    RowLists lists, rlists;
     size_t op_ws_bytes = 0;
     bool op_bound = false;
-    int64_t *d_lrow_base = nullptr;
-    int32_t *d_lrow_ptr = nullptr;
-    uint32_t *d_lent = nullptr;
 };
 
 namespace cheb {

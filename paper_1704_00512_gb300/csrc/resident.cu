@@ -51,6 +51,10 @@ struct ResArgs {
     const double *G;
     double *part;  // [panel][kmax][2] moment partials
     int32_t kmax;
+    // operator row lists of the resident panels (NULL: rank the operator rows)
+    const int64_t *lrow_base;
+    const int32_t *lrow_ptr;
+    const uint32_t *lent;
 };
 
 template <typename T>
@@ -230,6 +234,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_resident(const ResArgs<T> a) 
     const int q = lane % P, kg = lane / P;
     const unsigned lt = (1u << lane) - 1u;
     int2 *wl = wlist + warp * 64;
+    // With the plan's operator row lists the in-union entries of a row are read
+    // from its list (the same entries in the same order as ranking gives);
+    // otherwise the row's column indices are ranked against the bitmap.
+    const int32_t *rptr = a.lrow_ptr ? a.lrow_ptr + a.lrow_base[panel] : nullptr;
     for (int k = 1; k + 1 < n; ++k) {
         for (int s = warp; s < nu; s += NW) {
             const int I = ulist[s];
@@ -238,20 +246,30 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_resident(const ResArgs<T> a) 
 #pragma unroll
             for (int i = 0; i < 16; ++i) acc[i] = T(0);
             int pending = 0;
-            int64_t base = a0;
-            int Knext = (a0 + lane < a1) ? a.Lci[a0 + lane] : -1;
+            int64_t base = rptr ? (int64_t)rptr[s] : a0;
+            const int64_t end = rptr ? (int64_t)rptr[s + 1] : a1;
+            int Knext = (!rptr && a0 + lane < a1) ? a.Lci[a0 + lane] : -1;
+            uint32_t wnext = (rptr && base + lane < end) ? a.lent[base + lane] : 0u;
             while (true) {
-                if (base < a1) {
-                    const int K = Knext;
-                    Knext = (base + 32 + lane < a1) ? a.Lci[base + 32 + lane] : -1;
-                    const int s2 = K >= 0 ? rank_of(bits, K) : -1;
-                    const unsigned vm = __ballot_sync(0xffffffffu, s2 >= 0);
-                    if (s2 >= 0) wl[pending + __popc(vm & lt)] = make_int2((int)(base + lane), s2);
-                    pending += __popc(vm);
+                if (base < end) {
+                    if (rptr) {
+                        const int nn = end - base < 32 ? (int)(end - base) : 32;
+                        const uint32_t w = wnext;
+                        wnext = (base + 32 + lane < end) ? a.lent[base + 32 + lane] : 0u;
+                        if (lane < nn) wl[pending + lane] = make_int2((int)(a0 + (w >> 16)), (int)(w & 0xffffu));
+                        pending += nn;
+                    } else {
+                        const int K = Knext;
+                        Knext = (base + 32 + lane < a1) ? a.Lci[base + 32 + lane] : -1;
+                        const int s2 = K >= 0 ? rank_of(bits, K) : -1;
+                        const unsigned vm = __ballot_sync(0xffffffffu, s2 >= 0);
+                        if (s2 >= 0) wl[pending + __popc(vm & lt)] = make_int2((int)(base + lane), s2);
+                        pending += __popc(vm);
+                    }
                     base += 32;
                     __syncwarp();
                 }
-                const bool raw_done = base >= a1;
+                const bool raw_done = base >= end;
                 if (pending >= 32 || (raw_done && pending > 0)) {
                     const int nb = pending < 32 ? pending : 32;
                     int2 en[NU];
@@ -449,6 +467,11 @@ int resident_impl(const cheb_plan *plan, const cheb_bsr *Mt, int kmax, const int
     a.Lrp = Mt->row_ptr;
     a.Lci = Mt->col_idx;
     a.Lv = Lv;
+    if (plan->op_bound && plan->op_rp == Mt->row_ptr && plan->op_ci == Mt->col_idx && plan->rlists.d_ptr) {
+        a.lrow_base = plan->rlists.d_base;
+        a.lrow_ptr = plan->rlists.d_ptr;
+        a.lent = plan->rlists.d_ent;
+    }
     a.n_terms = n_terms_dev;
     a.n_single = n_single;
     a.coef = coeffs;

@@ -607,3 +607,31 @@ def test_selected_eigenvalues_counts_and_levels():
     assert relF(out["gmoments"].cpu().numpy(), ex.g) < 1e-10
     r = ref.mu_bisect(ex.g, ref.KIND_FERMI, kT, e0, e1, N - 0.5, 1e-10, 128)
     assert abs(out["eigenvalues"][0] - r.mu) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_resident_row_lists_bit_identical_to_ranking(prec):
+    # the one-launch (resident) expansion reads its in-union operator blocks
+    # from the plan's row lists when they are attached: same blocks, same
+    # order, so the same bits as ranking them at every step
+    n, nf = 40, 2
+    s, H, P_out, e0, e1, Ht, coeffs, G = _expand_case(120, 4.0, 2.0, 77, n, nf)
+    ex = ref.chebyshev_expand(Ht, P_out, coeffs, G=G)
+    dP = dbsr(P_out.row_ptr, P_out.col_idx)
+    dHt = dbsr(Ht.row_ptr, Ht.col_idx, Ht.vals)
+
+    def run(plan):
+        assert cg.plan_resident_info(plan)[0] > 0
+        acc = [torch.zeros((P_out.nnzb, 4, 4), dtype=torch.float64, device=DEV) for _ in range(nf)]
+        g = torch.zeros(n, dtype=torch.float64, device=DEV)
+        cg.expand(plan, dHt, n, torch.as_tensor(coeffs, device=DEV), acc, G=torch.as_tensor(G.vals, device=DEV),
+                  gmoments=g, precision=prec)
+        return acc, g
+
+    acc0, g0 = run(cg.Plan(dP, prec))
+    acc1, g1 = run(cg.Plan(dP, prec).attach_operator(dHt))
+    tol = 1e-10 if prec == cg.F64 else 1e-5
+    for j in range(nf):
+        assert torch.equal(acc1[j], acc0[j])
+        assert relF(acc1[j].cpu().numpy(), ex.acc[j].vals) < tol
+    assert torch.equal(g1, g0)
