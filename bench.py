@@ -34,6 +34,10 @@ import numpy as np  # noqa: E402
 METRIC = "density-matrix solves/s at <=1e-6 vs FP64 plain; masked SpGEMM HBM GB/s"
 UNIT = "solves/s"
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes per P_out block of one k_step<float, 4, 16, 1> launch (ncu on a
+# 4,000-atom system, profiles/k_step_f32_traffic_4000atoms.md): moment pass and
+# 4-accumulator pass.  Valid for that kernel version only.
+KSTEP_F32_DRAM_PER_BLOCK = {"moments": 642.1, "acc4": 1562.4}
 SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 
 WORKLOADS = {
@@ -332,6 +336,10 @@ def run_cheb(args, rank: int, world: int, local: int):
         roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(hbm_frac, 4), "traffic": None, "peak_source": f"{hbm_src} copy bandwidth"}
     roof["kernel"] = "k_step<float,4,16>" if prec == cg.F32 else "k_step<double,2,8>"
+    if prec == cg.F32 and not learned_form and cfg["n_mu"] == 4 and pb.planX.tile in (-1, 0):
+        per_block = 0.5 * (KSTEP_F32_DRAM_PER_BLOCK["moments"] + KSTEP_F32_DRAM_PER_BLOCK["acc4"])
+        roof["traffic"] = int(per_block * nnz_out)
+        roof["traffic_source"] = "ncu dram bytes per P_out block on 4,000 atoms, scaled by blocks"
     roof["algorithmic_bytes_per_launch"] = int((b1 + b2) / n_pass)
     roof["algorithmic_flops_per_launch"] = flops
     roof["avg_launch_ms"] = round((p1 + p2) / (n_pass * steps_per_pass), 5)
