@@ -60,6 +60,10 @@ WORKLOADS = {
     # The plain FP64 density matrix: 200 atoms x 4, 8 bohr cutoff, kT = 0.01, N_e = 400.
     "foe_fp64_800": dict(n_atoms=200, r_c=8.0, r_buf=4.0, kT=0.01, N_e=400.0, tol=1e-10, tol_S=1e-10,
                          precision="f64", n_mu=1),
+    # Matrix powers S^-1, S^1/2, S^-1/2 from one shared FP64 recursion: 3,000
+    # atoms x 4 (12,000 rows), 10 bohr cutoff, 4 bohr output buffer.
+    "powers_fp64_12k": dict(powers=True, n_atoms=3000, r_c=10.0, r_buf=4.0, tol=1e-10, precision="f64", n_mu=3,
+                            exponents=(-1.0, 0.5, -0.5)),
     # Batched: 64 independent systems of U{125..1500} atoms (seeds 0..63), 8 bohr
     # cutoff, each with its own bounds, degree and mu; both passes one launch
     # each, captured in CUDA graphs; autotuned tile shapes.
@@ -373,6 +377,91 @@ def run_cheb(args, rank: int, world: int, local: int):
         print(json.dumps(res), flush=True)
 
 
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (the FMA-loop probe measured 1.19)
+
+
+def run_powers(args, rank: int, world: int, local: int):
+    """Matrix powers: one step = S^a for every exponent from one FP64 recursion
+    (bounds, degree, coefficients and the expansion)."""
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_1704_00512_gb300 as cg
+    from paper_1704_00512_gb300 import solve
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = WORKLOADS[args.workload]
+    sysm = synth.make_system(cfg["n_atoms"], cfg["r_c"], seed=system_seed(rank))
+    pb = solve.problem_from_system(sysm, cfg["r_buf"], dev, cg.F64)
+
+    def step():
+        pb.build_patterns()
+        return solve.powers(pb, exponents=cfg["exponents"], tol=cfg["tol"], n_max=512)
+
+    for i in range(args.warmup):
+        out = step()
+        torch.cuda.synchronize()
+        log(f"[rank {rank}] warmup {i}: n_terms={out['n_terms']} bounds={out['bounds']}")
+    clk = ClockSampler(local, enabled=not args.no_clocks)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = cg.launch_count()
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        out = step()
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = cg.launch_count() - l0
+    t_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    value = job_throughput(args.steps, world, t_ms)
+    h_S = torch.from_numpy(np.ascontiguousarray(sysm.S)).pin_memory()
+    h_out = [torch.empty(tuple(a.shape), dtype=torch.float64).pin_memory() for a in out["acc"]]
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(args.e2e_steps):
+        pb.S.vals.copy_(h_S, non_blocking=True)
+        o = step()
+        for h, a in zip(h_out, o["acc"]):
+            h.copy_(a, non_blocking=True)
+    f1.record()
+    torch.cuda.synchronize()
+    te_ms = max_over_ranks(f0.elapsed_time(f1), world, dev)
+    n_terms = out["n_terms"]
+    triples = count_triples(pb.P_H.row_ptr.cpu().numpy(), pb.P_H.col_idx.cpu().numpy(),
+                            pb.P_out.row_ptr.cpu().numpy(), pb.P_out.col_idx.cpu().numpy())
+    # FLOPs of the n-2 recursion steps over the whole step time (bounds and
+    # coefficients included, so a lower bound on the kernel's rate)
+    tflops = 2.0 * 64.0 * triples * (n_terms - 2) / (t_ms / args.steps / 1e3) / 1e12
+    res = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "atoms_per_gpu": cfg["n_atoms"], "rows": 4 * cfg["n_atoms"],
+                   "r_c": cfg["r_c"], "r_buf": cfg["r_buf"], "exponents": list(cfg["exponents"]), "n_terms": n_terms,
+                   "fit_tol": cfg["tol"], "blocks_P_H": pb.P_H.nnzb, "blocks_P_out": pb.P_out.nnzb,
+                   "triples": triples, "l2": "inputs larger than L2 (no flush)"},
+        "roofline": {"bound": "alu", "achieved": round(tflops, 4), "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                     "frac": round(tflops / FP64_NOMINAL_TFLOPS, 4), "traffic": None,
+                     "kernel": "k_step<double,2,8>", "peak_source": "GB300 nominal FP64 (measured 1.19)"},
+        "e2e": {"value": round(job_throughput(args.e2e_steps, world, te_ms), 4), "unit": UNIT,
+                "h2d_bytes_per_step": int(h_S.numel() * 8), "d2h_bytes_per_step": int(sum(h.numel() for h in h_out) * 8)},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
 def batched_sizes(cfg) -> list[int]:
     rng = np.random.default_rng(0)
     return [int(x) for x in rng.integers(cfg["atoms_lo"], cfg["atoms_hi"] + 1, cfg["n_sys"])]
@@ -537,6 +626,30 @@ def run_reference(args, rank: int, world: int):
         return
     import synth
     cfg = WORKLOADS[args.workload]
+    if cfg.get("powers"):
+        from oracle import ref
+        sysm = synth.make_system(cfg["n_atoms"], cfg["r_c"], seed=0)
+        n_terms = max(ref.choose_degree(ref.Func(ref.KIND_POWER, a=a), 0.03, 3.1, cfg["tol"], 512, rel=True)
+                      for a in cfg["exponents"])
+        times = []
+        for i in range(args.warmup + args.steps):
+            t_step, _ = oracle_sample(sysm, cfg, 1)
+            if i >= args.warmup:
+                times.append(t_step)
+        t_solve = statistics.mean(times) * (n_terms - 2)
+        value = 1.0 / t_solve
+        conf = {"workload": args.workload, "atoms_per_gpu": cfg["n_atoms"], "rows": 4 * cfg["n_atoms"],
+                "n_terms": n_terms}
+        sample = (f"per bench step one FP64 oracle recursion step of the same system with {len(cfg['exponents'])} "
+                  f"accumulators, scaled by {n_terms - 2} steps")
+        res = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": conf,
+               "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": sample},
+               "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(res), flush=True)
+        return
     if cfg.get("batched"):
         value, t_solve, conf, sample = run_reference_batched(args, cfg)
         res = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -591,6 +704,8 @@ def main():
         run_reference(args, rank, world)
     elif WORKLOADS[args.workload].get("batched"):
         run_batched(args, rank, world, local)
+    elif WORKLOADS[args.workload].get("powers"):
+        run_powers(args, rank, world, local)
     else:
         run_cheb(args, rank, world, local)
 
