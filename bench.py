@@ -579,6 +579,14 @@ def oracle_sample(sysm, cfg, n_products: int = 1):
     return dt / n_products, len(ci)
 
 
+def oracle_threads() -> int:
+    """Threads the oracle's OpenMP loops use (OMP_NUM_THREADS, else one per host core)."""
+    try:
+        return max(1, int(os.environ["OMP_NUM_THREADS"]))
+    except (KeyError, ValueError):
+        return os.cpu_count() or 1
+
+
 def solve_step_equivalents(n_terms: int, n_S: int, nnz_out: int, nnz_H: int) -> float:
     """Recursion-step equivalents of one solve: two passes of n_terms-2 steps, the
     S^-1/2 expansion, and six P_out x P_out products (orthogonalisation, the trace
@@ -589,7 +597,7 @@ def solve_step_equivalents(n_terms: int, n_S: int, nnz_out: int, nnz_H: int) -> 
 def cpu_baseline(sysm, cfg, n_terms, n_S) -> dict:
     t_step, nnz_out = oracle_sample(sysm, cfg, 1)
     eq = solve_step_equivalents(n_terms, n_S, nnz_out, sysm.nnzb)
-    return {"value": 1.0 / (t_step * eq), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": 1.0 / (t_step * eq), "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
             "sample": f"1 FP64 recursion step of the same system timed ({t_step:.2f}s), scaled by "
                       f"{eq:.0f} step-equivalents per solve"}
 
@@ -645,7 +653,7 @@ def run_reference(args, rank: int, world: int):
         res = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": conf,
-               "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
                                 "sample": sample},
                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(res), flush=True)
@@ -655,7 +663,7 @@ def run_reference(args, rank: int, world: int):
         res = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": conf,
-               "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
                                 "sample": sample},
                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(res), flush=True)
@@ -679,7 +687,7 @@ def run_reference(args, rank: int, world: int):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "atoms_per_gpu": cfg["n_atoms"], "rows": 4 * cfg["n_atoms"],
                       "n_terms": n_terms, "n_S": n_S},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
                             "sample": f"per bench step one FP64 oracle recursion step of the same system, "
                                       f"scaled by {eq:.0f} step-equivalents per solve"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -1,0 +1,60 @@
+"""Host-side logic of bench.py and the shipped proposal weights (no GPU)."""
+
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from oracle import mlp as omlp  # noqa: E402
+
+
+def test_workloads_carry_what_their_arm_reads():
+    for name, cfg in bench.WORKLOADS.items():
+        assert cfg["precision"] in ("f32", "f64"), name
+        if cfg.get("batched"):
+            assert {"n_sys", "atoms_lo", "atoms_hi", "r_c", "r_buf", "kT", "tol", "tol_S"} <= set(cfg), name
+        elif cfg.get("powers"):
+            assert {"n_atoms", "r_c", "r_buf", "tol", "exponents", "n_mu"} <= set(cfg), name
+        else:
+            assert {"n_atoms", "r_c", "r_buf", "kT", "N_e", "tol", "tol_S", "n_mu"} <= set(cfg), name
+            if cfg.get("form") == "learned":
+                assert cfg["n_mu"] <= 8 and 0 < cfg["max_half_kT"] <= 1.0
+    assert bench.DEFAULT_WORKLOAD in bench.WORKLOADS
+
+
+def test_batched_sizes_are_seeded_and_in_range():
+    cfg = bench.WORKLOADS["foe_batched_64"]
+    a, b = bench.batched_sizes(cfg), bench.batched_sizes(cfg)
+    assert a == b and len(a) == cfg["n_sys"]
+    assert min(a) >= cfg["atoms_lo"] and max(a) <= cfg["atoms_hi"]
+
+
+def test_step_bytes_counts_each_stream_once():
+    # T_k, T_{k-1} read and T_{k+1} written, the operator, accumulators read and written, G read
+    assert bench.step_bytes(10, 4, 4, 0, False) == 10 * 16 * 4 * 3 + 4 * 16 * 4
+    assert bench.step_bytes(10, 4, 8, 2, True) == 10 * 16 * 8 * 3 + 4 * 16 * 8 + 10 * 16 * 8 * 2 * 2 + 10 * 16 * 8
+
+
+def test_oracle_threads_follow_omp_setting(monkeypatch):
+    monkeypatch.setenv("OMP_NUM_THREADS", "3")
+    assert bench.oracle_threads() == 3
+    monkeypatch.delenv("OMP_NUM_THREADS")
+    assert bench.oracle_threads() == (os.cpu_count() or 1)
+
+
+def test_shipped_proposal_weights_match_the_network():
+    path = os.path.join(ROOT, "paper_1704_00512_gb300", "weights", "mu_proposal.npz")
+    with np.load(path) as d:
+        theta = d["theta"]
+        X, xstar, scale = d["features"], d["xstar"], d["scale"]
+    assert theta.shape == (omlp.N_PARAMS,) and np.all(np.isfinite(theta))
+    # the FP64 restatement of the network on the stored training inputs gives
+    # finite outputs of the expected shape
+    out, _ = omlp.forward(theta.astype(np.float64), X[:8].astype(np.float64))
+    assert out.shape == (8, 2) and np.all(np.isfinite(out))
+    assert X.shape[1] == omlp.N_IN and len(xstar) == len(scale) == len(X)
