@@ -19,9 +19,11 @@ expanded panel by panel, no panel straddling two systems):
   6. pass 2: one batched launch accumulating every p_i, post-processing
      F = P_out(S^-1/2 P_out(p S^-1/2)) and Tr(F_i S_i) per system.
 
-Passes 4 and 6 are captured in CUDA graphs on the first solve and replayed on
-later solves of the same batch (same patterns, degrees and buffers; new H
-values, as in the iterations of a self-consistent loop).  The tile shape of
+The expansion of pass 4 and all of pass 6 are captured in CUDA graphs on the
+first solve and replayed on later solves of the same batch (same patterns,
+degrees and buffers; new H values, as in the iterations of a self-consistent
+loop); the bisections run outside the graphs, since each takes its system's
+bounds, kT and N_e as launch arguments.  The tile shape of
 the batched launch is chosen by `autotune_tile`, which times every shape of
 the library's table on the batch and caches the fastest.
 
@@ -242,10 +244,15 @@ def foe_batched(bp: BatchedProblem, kT: float, N_e: list[float], tol: float = 1e
     Hst = bp.P_H.with_vals(st["Hpt"])
     tolN = [1e-6 * n for n in N_e] if tol_N is None else tol_N
 
+    # The captured passes hold only launches whose arguments stay fixed for the
+    # batch (buffers, term counts); each system's bisection takes its bounds,
+    # kT and N_e as kernel arguments, which change with H, so it runs outside.
     def pass1():
         st["g"].zero_()
         L.expand_batched(st["planX"], Hst, kmax, st["nt"], None, None, 0, [], G=st["G"], gmoments=st["g"],
                          moment_stride=kmax, precision=bp.precision, ws=st["wsA"])
+
+    def searches():
         for i in range(nsys):
             L.mu_search(st["g"][i], nH[i], bH[i][0], bH[i][1], kind, kT, N_e[i], tolN[i], max_iter,
                         result=st["res"][i], ws=st["mws"][i])
@@ -267,6 +274,7 @@ def foe_batched(bp: BatchedProblem, kT: float, N_e: list[float], tol: float = 1e
         ev[0].record()
         pass1()
         ev[1].record()
+        searches()
         res = L.decode_mu_batch(st["res"])
         mus = [r["mu"] for r in res]
         _fill_pass2_coeffs(st, kind, kT, mus, bH, nH, dev)
@@ -286,6 +294,7 @@ def foe_batched(bp: BatchedProblem, kT: float, N_e: list[float], tol: float = 1e
         ev[0].record()
         gA.replay()
         ev[1].record()
+        searches()
         res = L.decode_mu_batch(st["res"])
         mus = [r["mu"] for r in res]
         _fill_pass2_coeffs(st, kind, kT, mus, bH, nH, dev)
@@ -296,6 +305,7 @@ def foe_batched(bp: BatchedProblem, kT: float, N_e: list[float], tol: float = 1e
         ev[0].record()
         pass1()
         ev[1].record()
+        searches()
         res = L.decode_mu_batch(st["res"])
         mus = [r["mu"] for r in res]
         _fill_pass2_coeffs(st, kind, kT, mus, bH, nH, dev)
