@@ -543,7 +543,7 @@ def run_batched(args, rank: int, world: int, local: int):
                    "atoms_range": [min(sizes), max(sizes)], "r_c": cfg["r_c"], "r_buf": cfg["r_buf"],
                    "kT": cfg["kT"], "n_terms_range": [min(out["n_terms"]), max(out["n_terms"])],
                    "blocks_P_out": bp.P_out.nnzb, "blocks_P_H": bp.P_H.nnzb, "tiles": out["tiles"],
-                   "graphs": "both passes captured and replayed", "l2": "inputs larger than L2 (no flush)"},
+                   "graphs": "expansions, post-processing and traces captured and replayed; bisections eager", "l2": "inputs larger than L2 (no flush)"},
         "roofline": {"bound": "alu", "achieved": round(tflops, 3), "peak": round(alu_peak, 3), "unit": "TFLOP/s",
                      "frac": round(tflops / alu_peak, 4), "traffic": None, "kernel": "k_resident (batched)",
                      "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"},
