@@ -159,6 +159,27 @@ int cheb_plan_info(const cheb_plan *plan, int64_t *n_panels, int32_t *panel_widt
  * path.  Both paths multiply the same blocks in the same order, so results
  * are bit-identical.  Attaching again replaces the lists. */
 int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, size_t *op_ws_bytes, void *stream);
+
+/* Column-order step kernel of reduced-precision plans.  For a CHEB_F32 or
+ * CHEB_BF16 plan, cheb_plan_attach_operator also builds the gather plan of a
+ * second per-step kernel that keeps T_k in column order (the blocks of each
+ * block column contiguous; columns are independent under Eq. 3, Sec.
+ * "Expansion in Chebyshev polynomials"): panels of up to 4 block columns
+ * whose union of row lists fits shared memory (at most 1023 rows), in column
+ * order; per union row its operator entries with K in the union (32-bit
+ * words: index of the operator block << 10 | union slot), padded to whole
+ * chunks of 8 with entries naming a zero block; the union rows of a panel
+ * dealt to the thread block's warps to balance their chunks, each warp's
+ * chunks stored as one stream; and the union slot of every P_out block (2
+ * bytes each).  After cheb_plan_bind_operator, cheb_expand_stepwise with
+ * that operator and an FP32/BF16 precision runs this kernel; it sums each
+ * block product in a different order from the ranking kernel, so results
+ * agree to rounding, and are bitwise reproducible run to run.  It is not
+ * built (and the ranking kernel runs) when one column's rows do not fit it
+ * or the operator has 2^22 - 1 blocks or more.  cheb_plan_col_info reports
+ * its panel count (0 when not built), largest union and total operator
+ * entries (padding included). */
+int cheb_plan_col_info(const cheb_plan *plan, int64_t *n_panels, int32_t *max_union, int64_t *n_entries);
 int cheb_plan_bind_operator(cheb_plan *plan, void *op_ws, size_t op_ws_bytes, void *stream);
 int cheb_plan_destroy(cheb_plan *plan);
 
@@ -184,6 +205,14 @@ int cheb_bounds_workspace_size(int64_t nbr, int32_t k, size_t *bytes);
 int cheb_bounds(const cheb_bsr *M, int32_t k, const double *v0, double margin_frac,
                 double *emin, double *emax, double *theta, void *ws, size_t ws_bytes,
                 void *stream);
+
+/* Bounds of an SPD matrix for the matrix powers (Sec. "Matrix powers"): as
+ * cheb_bounds, then CHEB_ERR_NOT_SPD if the lowest Ritz value is <= 0, and the
+ * lower bound raised to at least half the lowest Ritz value (the paper's
+ * rescaling near zero is not specified; this keeps x^a finite on the
+ * interval).  Host-returning; same workspace as cheb_bounds. */
+int cheb_bounds_spd(const cheb_bsr *S, int32_t k, const double *v0, double margin_frac,
+                    double *emin, double *emax, void *ws, size_t ws_bytes, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Coefficients (Eq. 4) and degree (Eq. 6).  For each of the n_f functions
@@ -323,6 +352,20 @@ int cheb_trace(const cheb_bsr *A, const cheb_bsr *B, double *out, void *ws, size
 int cheb_penalty_trace(const double *moments, int32_t n_terms, double alpha, double *out,
                        void *ws, size_t ws_bytes, void *stream);
 
+/* The same trace as a decision on the solve path (host-returning): *value
+ * (host, may be NULL) = the penalty trace of the first n_terms (>= 3)
+ * moments; *verdict (host) = 0 when |value| < threshold; otherwise the side
+ * that fails, read from the last two moments: a level outside [-1, 1]
+ * dominates them as T_k grows like cosh(k acosh|x~|), with alternating signs
+ * below -1 (verdict -1: the lower bound is too high) and one sign above +1
+ * (verdict +1: the upper bound is too low) -- the sign of the trace itself
+ * does not tell, because the penalty polynomial grows outside the interval
+ * too; 2 when the trace or those moments are not finite (the recursion
+ * overflowed; no side named).  The threshold and alpha are the caller's (the
+ * paper leaves both open).  Workspace: 8*n_terms + 8 bytes. */
+int cheb_penalty_check(const double *moments, int32_t n_terms, double alpha, double threshold,
+                       double *value, int32_t *verdict, void *ws, size_t ws_bytes, void *stream);
+
 /* ---------------------------------------------------------------------------
  * mu search (Sec. "Fermi Operator Expansion": adjust mu until Tr(KS) = N, by
  * re-summing the expansion with new coefficients).  gmoments: device
@@ -400,6 +443,15 @@ int cheb_newton_schulz_isqrt(const cheb_plan *plan, const cheb_bsr *S, const dou
  */
 int cheb_lincomb(int32_t n, const double *weights, const double *const *x, int64_t len, double *out,
                  void *stream);
+
+/* Several mu from one expansion (host arithmetic, no device work): the n
+ * Chebyshev points center + half*cos(pi (i+1/2)/n) of a bracket
+ * (cheb_mu_nodes), and the Lagrange weights of those points at x
+ * (cheb_lagrange_weights: weights[i] = prod_{j != i} (x - n_j)/(n_i - n_j)),
+ * so that F(x) ~ sum_i weights[i] F(n_i) through cheb_lincomb.  n <= 64.
+ * Errors: CHEB_ERR_INVALID for n out of range, half < 0, repeated nodes. */
+int cheb_mu_nodes(double center, double half, int32_t n, double *nodes);
+int cheb_lagrange_weights(const double *nodes, int32_t n, double x, double *weights);
 
 /* ---------------------------------------------------------------------------
  * Learned mu proposal (not in the paper).  A 35 -> 128 -> 128 -> 2 ReLU network

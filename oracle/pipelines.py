@@ -39,7 +39,7 @@ def powers(S: ref.Bsr, P_out: ref.Bsr, exponents, bounds, n_terms: int, newton_s
 
 
 def foe(S: ref.Bsr, H: ref.Bsr, P_out: ref.Bsr, kT: float, N_e: float, bounds_S, n_S: int, bounds_H, n_H: int,
-        tol_N: float, kind: int = ref.KIND_FERMI, max_iter: int = 100, colmask=None):
+        tol_N: float, kind: int = ref.KIND_FERMI, max_iter: int = 100):
     """FOE with the S^-1/2 transformation and bisection on the trace functional."""
     A = powers(S, P_out, (-0.5,), bounds_S, n_S)["acc"][0]
     Hp = ref.orthogonalise(H, A, P_out)

@@ -56,6 +56,9 @@ def _load():
         lib.oracle_spmv.argtypes = [ctypes.c_int64, p, p, p, p, p]
         lib.oracle_spmv.restype = None
         lib.oracle_pattern.argtypes = [ctypes.c_int64, p, ctypes.c_double, ctypes.c_double, p, p]
+        lib.oracle_column_expand.argtypes = [ctypes.c_int64, p, p, p, p, p, ctypes.c_int64, p, ctypes.c_int64,
+                                             ctypes.c_int64, p, p]
+        lib.oracle_column_expand.restype = None
         lib.oracle_pattern.restype = None
         _lib = lib
     return _lib
@@ -457,6 +460,43 @@ def chebyshev_expand(Mt: Bsr, P_out: Bsr, coeffs: np.ndarray, G: Bsr | None = No
             g[:] = np.nan
     ex = Expansion(acc=acc, t=t, g=g)
     return (ex, Ts) if keep_T else ex
+
+
+def column_expand(Mt: Bsr, P_out: Bsr, cols, coeffs: np.ndarray) -> list[list[np.ndarray]]:
+    """The accumulators of Eq. 1 on the sampled block columns only (by Eq. 3's
+    column independence, Sec. "Expansion in Chebyshev polynomials"): result
+    [f][c] = array [rows of column cols[c], 4, 4], the blocks (I, cols[c]) of
+    acc_f in ascending I (the column list of row cols[c] of the symmetric
+    P_out).  Same recursion as chebyshev_expand, run in liboracle.c per column."""
+    coeffs = np.ascontiguousarray(np.atleast_2d(np.asarray(coeffs, dtype=np.float64)))
+    nf, n = coeffs.shape
+    cols = np.ascontiguousarray(np.asarray(cols, dtype=np.int32))
+    lens = [int(P_out.row_ptr[j + 1] - P_out.row_ptr[j]) for j in cols]
+    total = int(sum(lens))
+    out = np.zeros((nf, total, 4, 4))
+    lib = _load()
+    lib.oracle_column_expand(Mt.nbr, _ptr(np.ascontiguousarray(Mt.row_ptr, dtype=np.int64)),
+                             _ptr(np.ascontiguousarray(Mt.col_idx, dtype=np.int32)),
+                             _ptr(np.ascontiguousarray(Mt.vals, dtype=np.float64)),
+                             _ptr(np.ascontiguousarray(P_out.row_ptr, dtype=np.int64)),
+                             _ptr(np.ascontiguousarray(P_out.col_idx, dtype=np.int32)), len(cols), _ptr(cols), n, nf,
+                             _ptr(coeffs), _ptr(out))
+    res, off = [], np.concatenate([[0], np.cumsum(lens)])
+    for f in range(nf):
+        res.append([out[f, off[c]:off[c + 1]] for c in range(len(cols))])
+    return res
+
+
+def column_blocks(A: np.ndarray, P_out: Bsr, cols) -> list[np.ndarray]:
+    """The blocks (I, J) of a P_out-valued array A (BCSR order) for each J in
+    cols, in ascending I: the layout of column_expand's result."""
+    out = []
+    for J in cols:
+        rows = P_out.col_idx[P_out.row_ptr[J]:P_out.row_ptr[J + 1]]
+        idx = [P_out.row_ptr[I] + int(np.searchsorted(P_out.col_idx[P_out.row_ptr[I]:P_out.row_ptr[I + 1]], J))
+               for I in rows]
+        out.append(np.asarray(A)[idx])
+    return out
 
 
 # ----------------------------------------------------------------------------

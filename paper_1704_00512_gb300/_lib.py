@@ -33,6 +33,7 @@ EXPORTS = [
     "cheb_mlp_forward", "cheb_mlp_loss", "cheb_mlp_backward", "cheb_mlp_adam", "cheb_mlp_features",
     "cheb_masked_product", "cheb_transpose", "cheb_restrict", "cheb_trace_workspace_size", "cheb_trace",
     "cheb_penalty_trace", "cheb_mu_search", "cheb_mu_search_noalloc", "cheb_newton_schulz", "cheb_newton_schulz_isqrt",
+    "cheb_plan_col_info", "cheb_penalty_check", "cheb_mu_nodes", "cheb_lagrange_weights", "cheb_bounds_spd",
 ]
 
 
@@ -90,6 +91,11 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
         "cheb_expand_stepwise": ([p, P(CBsr), i32, p, i32, i32, P(p), p, p, p, i32, p, sz, p], i32),
         "cheb_plan_create_batched": ([P(CBsr), i32, i32, i32, P(i64), P(p), P(sz), p], i32),
         "cheb_plan_resident_info": ([p, P(i64), P(i32), P(i32)], i32),
+        "cheb_plan_col_info": ([p, P(i64), P(i32), P(i64)], i32),
+        "cheb_penalty_check": ([p, i32, dbl, dbl, P(dbl), P(i32), p, sz, p], i32),
+        "cheb_mu_nodes": ([dbl, dbl, i32, P(dbl)], i32),
+        "cheb_lagrange_weights": ([P(dbl), i32, dbl, P(dbl)], i32),
+        "cheb_bounds_spd": ([P(CBsr), i32, p, dbl, P(dbl), P(dbl), p, sz, p], i32),
         "cheb_expand_batched": ([p, P(CBsr), i32, p, p, p, i32, i32, P(p), p, p, p, i32, i32, p, sz, p], i32),
         "cheb_block_diag": ([i32, P(CBsr), p, p, p, i32, p], i32),
         "cheb_lincomb": ([i32, P(dbl), P(p), i64, p, p], i32),
@@ -346,6 +352,13 @@ class BatchedPlan(Plan):
         _check(lib.cheb_plan_bind(h, ctypes.c_void_p(_aligned(self._ws)), nbytes.value, s))
 
 
+def plan_col_info(plan: Plan) -> tuple[int, int, int]:
+    """cheb_plan_col_info: (panels, largest union, operator entries) of the column-order step kernel (0 panels: not built)."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+    _check(load().cheb_plan_col_info(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
 def plan_resident_info(plan: Plan) -> tuple[int, int, int]:
     a, b, c = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
     _check(load().cheb_plan_resident_info(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
@@ -430,6 +443,45 @@ def trace(A: Bsr, B: Bsr, out: torch.Tensor | None = None, stream=None, ws: torc
     _check(lib.cheb_trace(ctypes.byref(ca), ctypes.byref(cbb), _ptr(out), ctypes.c_void_p(_aligned(ws)), nb.value,
                           _stream(stream)))
     return out
+
+
+def penalty_check(moments: torch.Tensor, n_terms: int, alpha: float, threshold: float, stream=None):
+    """cheb_penalty_check: (verdict, value); verdict 0 ok, -1 lower bound, +1 upper bound, 2 not finite."""
+    ws = _ws(8 * n_terms + 8, moments.device)
+    v, d = ctypes.c_double(0.0), ctypes.c_int32(0)
+    _check(load().cheb_penalty_check(_ptr(moments), n_terms, alpha, threshold, ctypes.byref(v), ctypes.byref(d),
+                                     ctypes.c_void_p(_aligned(ws)), 8 * n_terms + 8, _stream(stream)))
+    return d.value, v.value
+
+
+def mu_nodes(center: float, half: float, n: int) -> list[float]:
+    """cheb_mu_nodes: Chebyshev points of the bracket [center - half, center + half]."""
+    out = (ctypes.c_double * n)()
+    _check(load().cheb_mu_nodes(center, half, n, out))
+    return list(out)
+
+
+def lagrange_weights(nodes, x: float) -> list[float]:
+    """cheb_lagrange_weights."""
+    n = len(nodes)
+    a = (ctypes.c_double * n)(*[float(v) for v in nodes])
+    out = (ctypes.c_double * n)()
+    _check(load().cheb_lagrange_weights(a, n, x, out))
+    return list(out)
+
+
+def bounds_spd(S: Bsr, k: int = 40, v0: torch.Tensor | None = None, margin_frac: float = 0.01,
+               stream=None) -> tuple[float, float]:
+    """cheb_bounds_spd: Lanczos bounds with the SPD check and the lower-bound clamp."""
+    lib = load()
+    nb = ctypes.c_size_t(0)
+    _check(lib.cheb_bounds_workspace_size(S.nbr, k, ctypes.byref(nb)))
+    ws = _ws(nb.value, S.vals.device)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    cb = S.c()
+    _check(lib.cheb_bounds_spd(ctypes.byref(cb), k, _ptr(v0), margin_frac, ctypes.byref(lo), ctypes.byref(hi),
+                               ctypes.c_void_p(_aligned(ws)), nb.value, _stream(stream)))
+    return lo.value, hi.value
 
 
 def penalty_trace(moments: torch.Tensor, n_terms: int, alpha: float, stream=None) -> torch.Tensor:

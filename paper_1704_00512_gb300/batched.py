@@ -163,11 +163,7 @@ def prepare_batched(bp: BatchedProblem, kT, tol: float = 1e-7, tol_S: float = 1e
     # --- S^-1/2 of every system: one batched FP64 power expansion
     bS = []
     for i in range(nsys):
-        Si = _slice_bsr(bp.PH[i], bp.S.vals, bp.hoff[i])
-        e0, e1, th = L.bounds(Si, lanczos_k)
-        if th[0] <= 0:
-            raise L.ChebError(L.ERR_NOT_SPD, f"system {i}: Lanczos lower Ritz value {th[0]} <= 0")
-        bS.append((max(e0, 0.5 * th[0]), e1))
+        bS.append(L.bounds_spd(_slice_bsr(bp.PH[i], bp.S.vals, bp.hoff[i]), lanczos_k))
     St = torch.empty_like(bp.S.vals)
     for i in range(nsys):
         L.scale(_slice_bsr(bp.PH[i], bp.S.vals, bp.hoff[i]), *bS[i], out=St[bp.hoff[i]:bp.hoff[i + 1]])

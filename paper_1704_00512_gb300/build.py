@@ -19,6 +19,10 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcheb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+# Sources whose kernels must compile without register spills (the column-order
+# step kernel keeps L2 cache-policy values in registers; its shape is chosen
+# so that they never go to local memory).
+NO_SPILL = {"colstep.cu"}
 
 
 def _nvcc() -> str:
@@ -53,9 +57,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        if os.path.basename(src) in NO_SPILL:
+            cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        if os.path.basename(src) in NO_SPILL:
+            spills = [ln for ln in r.stderr.splitlines() if "spill stores" in ln and not ln.strip().startswith("0 bytes")
+                      and " 0 bytes spill stores" not in ln]
+            if spills:
+                raise RuntimeError(f"{src}: register spills in a kernel built to run without them:\n" + "\n".join(spills))
         if verbose and r.stderr:
             print(r.stderr)
         return obj

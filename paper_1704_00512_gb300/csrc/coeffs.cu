@@ -404,3 +404,62 @@ extern "C" int cheb_mu_search_noalloc(const double *gmoments, int32_t n_terms, d
                                      static_cast<MuResult *>(result));
     return check_launch("k_bisect");
 }
+
+// ---------------------------------------------------------------------------
+// Scalar steps of the solve sequences, kept in the library so that the
+// binding only moves arguments.
+
+extern "C" int cheb_penalty_check(const double *moments, int32_t n_terms, double alpha, double threshold,
+                                  double *value, int32_t *verdict, void *ws, size_t ws_bytes, void *stream) {
+    if (!moments || n_terms < 3 || !(threshold > 0) || !verdict)
+        return fail(CHEB_ERR_INVALID, "cheb_penalty_check: bad arguments");
+    if (!ws || ws_bytes < (size_t)n_terms * 8 + 8) return fail(CHEB_ERR_NOSPACE, "cheb_penalty_check: workspace");
+    double *out = static_cast<double *>(ws) + n_terms;
+    CHEB_TRY(cheb_penalty_trace(moments, n_terms, alpha, out, ws, (size_t)n_terms * 8, stream));
+    double v = 0.0, last[2] = {0.0, 0.0};
+    cudaStream_t s = as_stream(stream);
+    CHEB_CUDA(cudaMemcpyAsync(&v, out, 8, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaMemcpyAsync(last, moments + n_terms - 2, 16, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaStreamSynchronize(s));
+    if (value) *value = v;
+    // A level outside [-1, 1] makes T_k grow like cosh(k acosh|x~|), and the
+    // penalty polynomial grows with it outside the interval, so |trace| says
+    // that a bound fails but its sign does not say which.  The moments do: the
+    // level's term dominates them, with one sign above +1 and alternating
+    // signs (T_k(-y) = (-1)^k T_k(y)) below -1.
+    const bool finite = v == v && v - v == 0.0 && last[0] - last[0] == 0.0 && last[1] - last[1] == 0.0;
+    if (!finite) *verdict = 2;
+    else if (fabs(v) < threshold) *verdict = 0;
+    else *verdict = last[0] * last[1] < 0.0 ? -1 : 1;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_mu_nodes(double center, double half, int32_t n, double *nodes) {
+    if (n < 1 || n > 64 || !nodes || !(half >= 0)) return fail(CHEB_ERR_INVALID, "cheb_mu_nodes: bad arguments");
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) nodes[i] = center + half * cos(pi * (i + 0.5) / n);
+    return CHEB_OK;
+}
+
+extern "C" int cheb_lagrange_weights(const double *nodes, int32_t n, double x, double *weights) {
+    if (n < 1 || n > 64 || !nodes || !weights) return fail(CHEB_ERR_INVALID, "cheb_lagrange_weights: bad arguments");
+    for (int i = 0; i < n; ++i) {
+        double v = 1.0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            if (nodes[i] == nodes[j]) return fail(CHEB_ERR_INVALID, "cheb_lagrange_weights: repeated node");
+            v *= (x - nodes[j]) / (nodes[i] - nodes[j]);
+        }
+        weights[i] = v;
+    }
+    return CHEB_OK;
+}
+
+extern "C" int cheb_bounds_spd(const cheb_bsr *S, int32_t k, const double *v0, double margin_frac, double *emin,
+                               double *emax, void *ws, size_t ws_bytes, void *stream) {
+    double th[2];
+    CHEB_TRY(cheb_bounds(S, k, v0, margin_frac, emin, emax, th, ws, ws_bytes, stream));
+    if (!(th[0] > 0)) return fail(CHEB_ERR_NOT_SPD, "cheb_bounds_spd: lowest Ritz value %g <= 0", th[0]);
+    if (*emin < 0.5 * th[0]) *emin = 0.5 * th[0];
+    return CHEB_OK;
+}

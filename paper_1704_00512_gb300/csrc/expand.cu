@@ -661,7 +661,9 @@ size_t expand_ws(const cheb_plan *plan, int64_t nnzL, int precision) {
     size_t b = 3 * align_up(plan->nnzb * BB * esz);
     if (precision != CHEB_F64) b += align_up(nnzL * BB * esz);
     b += align_up(plan->n_panels * 4 * sizeof(double)) + align_up(64);
-    return b + 256;
+    b += 256;
+    if (precision != CHEB_F64 && plan->col.built) b = std::max(b, col_expand_ws(plan, nnzL));
+    return b;
 }
 
 template <typename T>
@@ -747,6 +749,9 @@ extern "C" int cheb_expand_stepwise(const cheb_plan *plan, const cheb_bsr *Mt, i
     if (precision == CHEB_F64)
         return expand_impl<double>(plan, Mt, n_terms, coeffs, coeff_stride, n_f, acc, moments, G, gmoments, ws,
                                    ws_bytes, s);
+    if ((precision == CHEB_F32 || precision == CHEB_BF16) && col_usable(plan, Mt))
+        return col_expand(plan, Mt, n_terms, coeffs, coeff_stride, n_f, acc, moments, G, gmoments, ws, ws_bytes, s,
+                          precision == CHEB_BF16);
     if (precision == CHEB_F32 || precision == CHEB_BF16)
         return expand_impl<float>(plan, Mt, n_terms, coeffs, coeff_stride, n_f, acc, moments, G, gmoments, ws,
                                   ws_bytes, s, precision == CHEB_BF16);

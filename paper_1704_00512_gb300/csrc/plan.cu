@@ -272,6 +272,16 @@ extern "C" int cheb_plan_resident_info(const cheb_plan *plan, int64_t *n_panels,
     return CHEB_OK;
 }
 
+extern "C" int cheb_plan_col_info(const cheb_plan *plan, int64_t *n_panels, int32_t *max_union,
+                                  int64_t *n_entries) {
+    if (!plan) return fail(CHEB_ERR_INVALID, "cheb_plan_col_info: NULL plan");
+    const bool on = plan->col.built;
+    if (n_panels) *n_panels = on ? plan->col.n_panels : 0;
+    if (max_union) *max_union = on ? plan->col.max_union : 0;
+    if (n_entries) *n_entries = on ? plan->col.n_entries : 0;
+    return CHEB_OK;
+}
+
 extern "C" int cheb_plan_destroy(cheb_plan *plan) {
     delete plan;
     return CHEB_OK;
@@ -386,7 +396,15 @@ extern "C" int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, siz
     plan->op_ci = L->col_idx;
     plan->lists = std::move(lists);
     plan->rlists = std::move(rlists);
-    plan->op_ws_bytes = plan->lists.bytes() + plan->rlists.bytes();
+    // reduced-precision plans: the column-order step kernel's lists (left
+    // unbuilt when a panel column or an operator row does not fit it; the
+    // per-step products then use the ranking kernel)
+    plan->col = ColLists();
+    if (plan->precision != CHEB_F64) {
+        const int rc = col_build(plan, rp, ci, lrp, lci);
+        if (rc != CHEB_OK && rc != CHEB_ERR_NOSPACE) return rc;
+    }
+    plan->op_ws_bytes = plan->lists.bytes() + plan->rlists.bytes() + plan->col.bytes();
     plan->op_bound = false;
     *op_ws_bytes = plan->op_ws_bytes;
     return CHEB_OK;
@@ -415,7 +433,9 @@ extern "C" int cheb_plan_bind_operator(cheb_plan *plan, void *ws, size_t ws_byte
     cudaStream_t s = as_stream(stream);
     CHEB_TRY(bind_row_lists(plan->lists, cv, s));
     CHEB_TRY(bind_row_lists(plan->rlists, cv, s));
+    CHEB_TRY(col_bind(plan->col, cv, s));
     CHEB_CUDA(cudaStreamSynchronize(s));
+    col_release_host(plan->col);
     // the device copies are the only ones needed from here on
     for (RowLists *l : {&plan->lists, &plan->rlists}) {
         std::vector<int32_t>().swap(l->h_ptr);

@@ -24,6 +24,41 @@ struct RowLists {
     }
 };
 
+// Data of the column-order step kernel (colstep.cu) for one operator pattern:
+// its own panels (at most COL_P columns whose union fits shared memory), in
+// column order, as (first column, column count, union rows, 0); per panel and
+// warp a range of chunks and of rows; per warp row a word (union slot, a flag
+// for rows with blocks in at most two of the panel's columns and those
+// columns, chunk count); the chunks' entry words (index of the block L_IK in the
+// operator << COL_SLOT_BITS | union slot of K; COL_EK * 32/COL_P words per
+// chunk, word e * 32/COL_P + g for K-group g); and
+// the union slot of every P_out block in column order.
+struct ColLists {
+    int32_t P = 0, NW = 0;
+    int32_t ucap = 0, max_union = 0, max_row = 0;
+    int64_t n_panels = 0;
+    int64_t n_entries = 0;  // padded, in whole chunks
+    std::vector<int32_t> h_panels;
+    std::vector<int32_t> h_wchunk;  // [panels][NW + 1]
+    std::vector<int32_t> h_wrow;    // [panels][NW + 1]
+    std::vector<uint32_t> h_rows;
+    std::vector<uint32_t> h_ent;
+    std::vector<uint16_t> h_slot;
+    int32_t *d_panels = nullptr;
+    int32_t *d_wchunk = nullptr;
+    int32_t *d_wrow = nullptr;
+    uint32_t *d_rows = nullptr;
+    uint32_t *d_ent = nullptr;
+    uint16_t *d_slot = nullptr;
+    bool built = false, bound = false;
+    size_t bytes() const {
+        if (!built) return 0;
+        return ::cheb::align_up(h_panels.size() * 4) + ::cheb::align_up(h_wchunk.size() * 4) +
+               ::cheb::align_up(h_wrow.size() * 4) + ::cheb::align_up(std::max<size_t>(h_rows.size(), 1) * 4) +
+               ::cheb::align_up(std::max<size_t>(h_ent.size(), 1) * 4) + ::cheb::align_up(h_slot.size() * 2);
+    }
+};
+
 struct cheb_plan {
     int64_t nbr = 0;
     int64_t nnzb = 0;
@@ -66,6 +101,7 @@ struct cheb_plan {
     const int64_t *op_rp = nullptr;
     const int32_t *op_ci = nullptr;
     RowLists lists, rlists;
+    ColLists col;  // FP32 / BF16 plans: the column-order step kernel's lists
     size_t op_ws_bytes = 0;
     bool op_bound = false;
 };
@@ -147,6 +183,39 @@ __host__ __device__ inline ResLayout res_layout(int64_t nw, int64_t ucap, int64_
     return L;
 }
 
+// Column-order step kernel (colstep.cu): panel width, warps, operator stages
+// per warp, and its shared-memory layout for a union of ucap rows: the warps'
+// stages of operator blocks, the panel's T_k blocks X[slot][4][4P] (FP32),
+// the column-order position of each (union row, panel column) block, the
+// moment partials of the warps.
+constexpr int COL_P = 4;
+constexpr int COL_NW = 16;
+constexpr int COL_STAGES = 3;
+constexpr int COL_EK = 2;  // operator entries of each K-group per chunk
+constexpr int COL_SLOT_BITS = 10;  // union slots < 1024; operator blocks < 2^22
+// a row word: union slot | half-row flag << 10 | its two columns << 11, << 13
+// | chunk count << COL_ROW_SHIFT
+constexpr int COL_ROW_SHIFT = COL_SLOT_BITS + 5;
+struct ColLayout {
+    size_t off_x, off_pos, off_stage, off_red, total;
+};
+__host__ __device__ inline ColLayout col_layout(int64_t ucap, int P, int nwarps) {
+    ColLayout L;
+    const int kg = 32 / P;
+    size_t o = 0;
+    L.off_stage = o;  // per warp: COL_STAGES chunks of COL_EK * 32/P operator blocks
+    o += (size_t)nwarps * COL_STAGES * COL_EK * kg * 64;
+    L.off_x = o;
+    o += (size_t)ucap * 64 * P;
+    L.off_pos = o;
+    o += (size_t)ucap * P * 4;
+    o = (o + 15) / 16 * 16;
+    L.off_red = o;
+    o += (size_t)nwarps * 6 * 8;  // moment partials: 6 per warp
+    L.total = o;
+    return L;
+}
+
 // Tile shapes of the step kernel: panel width P, warps per block NW, blocks per
 // SM MINB (the shared-memory budget of a block is the SM's share for MINB).
 struct TileCfg {
@@ -166,5 +235,17 @@ inline size_t smem_budget(int minb) {
     size_t per = 233472 / (size_t)minb - 1024 - 512;
     return per < (size_t)CHEB_MAX_DYN_SMEM ? per : (size_t)CHEB_MAX_DYN_SMEM;
 }
+
+// Column-order step kernel (colstep.cu): host build and binding of its lists,
+// and the expansion through it.
+int col_build(cheb_plan *plan, const std::vector<int64_t> &rp, const std::vector<int32_t> &ci,
+              const std::vector<int64_t> &lrp, const std::vector<int32_t> &lci);
+int col_bind(ColLists &c, Carve &cv, cudaStream_t s);
+void col_release_host(ColLists &c);
+bool col_usable(const cheb_plan *plan, const cheb_bsr *Mt);
+size_t col_expand_ws(const cheb_plan *plan, int64_t nnzL);
+int col_expand(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_terms, const double *coeffs, int32_t stride,
+               int32_t nf, double *const *acc, double *moments, const double *G, double *gmoments, void *ws,
+               size_t ws_bytes, cudaStream_t s, int round_bf16);
 
 }  // namespace cheb

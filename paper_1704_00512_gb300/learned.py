@@ -164,21 +164,6 @@ def load_proposal(device, path: str = WEIGHTS) -> Proposal:
     return Proposal(theta, device)
 
 
-def chebyshev_nodes(center: float, half: float, n: int) -> list[float]:
-    return [center + half * math.cos(math.pi * (i + 0.5) / n) for i in range(n)]
-
-
-def lagrange_weights(nodes: list[float], x: float) -> list[float]:
-    w = []
-    for i, xi in enumerate(nodes):
-        v = 1.0
-        for j, xj in enumerate(nodes):
-            if j != i:
-                v *= (x - xj) / (xi - xj)
-        w.append(v)
-    return w
-
-
 def foe_learned(pb: solve.Problem, prop: Proposal, kT: float, N_e: float, tol: float = 1e-7, n_mu: int = 8,
                 min_half_kT: float = 0.05, max_half_kT: float = 1.0, tol_N: float | None = None,
                 prepared=None, bracket: tuple[float, float] | None = None, stepwise: bool = True,
@@ -200,7 +185,7 @@ def foe_learned(pb: solve.Problem, prop: Proposal, kT: float, N_e: float, tol: f
         half = min(max(half, min_half_kT * kT), max_half_kT * kT)
     else:
         mu_hat, half = bracket
-    mus = chebyshev_nodes(mu_hat, half, n_mu)
+    mus = L.mu_nodes(mu_hat, half, n_mu)
     # same term count as the plain solve (degree chosen at the interval centre)
     n, _ = L.coeffs([{"kind": L.FERMI, "mu": tau, "kT": kT}], e0, e1, tol, 16384, device=pb.device)
     _, c = L.coeffs([{"kind": L.FERMI, "mu": m, "kT": kT} for m in mus], e0, e1, 0.0, n, device=pb.device)
@@ -218,7 +203,7 @@ def foe_learned(pb: solve.Problem, prop: Proposal, kT: float, N_e: float, tol: f
     p = pb.zeros_out()
     ev[2].record()
     if abs(mu - mu_hat) <= half:
-        L.lincomb(lagrange_weights(mus, mu), accs, p)
+        L.lincomb(L.lagrange_weights(mus, mu), accs, p)
     else:
         _, c2 = L.coeffs([{"kind": L.FERMI, "mu": mu, "kT": kT}], e0, e1, 0.0, n, device=pb.device)
         L.expand(pb.planX, Hpt, n, c2, [p], precision=pb.precision, ws=ws, stepwise=stepwise)

@@ -1,21 +1,31 @@
 """Solve sequences built from the C ABI (every numerical step runs in libcheb.so).
 
-``powers_solve``: matrix powers S^a from one shared recursion (Sec. "Matrix
+``powers``: matrix powers S^a from one shared recursion (Sec. "Matrix
 powers"), optionally followed by one FP64 Newton-Schulz step for S^-1.
 
-``foe_solve``: the Fermi-operator expansion with the S^-1/2 transformation and
-the mu search (Sec. "Fermi Operator Expansion"):
+``foe``: the Fermi-operator expansion with the S^-1/2 transformation and the
+mu search (Sec. "Fermi Operator Expansion"):
   1. block patterns P_H (cutoff r_c) and P_out (r_c + r_buf) from the atoms;
-  2. S^-1/2 by a power expansion of S on P_out;
+  2. S^-1/2 by a power expansion of S on P_out, and the trace functional
+     G = (P_out(S^-1/2 P_out(S S^-1/2)))^T, so that Tr(F(mu) S) =
+     sum_k c_k(mu) <T_k, G> (``overlap_setup``: both depend on S only, so a
+     sequence of solves with one overlap matrix computes them once);
   3. H' = P_H(S^-1/2 P_out(H S^-1/2));
   4. Lanczos bounds of H', degree for the occupation function at the interval
      centre (the hardest position for a Chebyshev fit);
-  5. pass 1: the recursion on H~' with the trace functional g_k = <T_k, G>,
-     G = (P_out(S^-1/2 P_out(S S^-1/2)))^T, so that Tr(F(mu) S) = sum_k c_k(mu) g_k;
+  5. pass 1: the recursion on H~' collecting Tr T_k (for the penalty check of
+     Eq. 5, which widens a failing bound once and otherwise reports
+     CHEB_ERR_BOUNDS) and g_k = <T_k, G>;
   6. bisection for Tr(F S) = N_e on g (no new products);
-  7. pass 2: the recursion again, accumulating p at mu* (and, with n_mu = 4,
-     at three more mu of a 4-point stencil around it);
-  8. F = P_out(S^-1/2 P_out(p S^-1/2)) and Tr(F S).
+  7. pass 2: the recursion again, accumulating p at mu*;
+  8. F = P_out(S^-1/2 P_out(p S^-1/2)) and Tr(FS).
+The form "mu4" runs pass 1 over the first half of the terms only; the
+bisection on those moments brackets mu* (the truncated series is a smoothed
+Fermi function of the same filling), pass 2 accumulates p at the 4 Chebyshev
+points of a bracket of half-width mu_half_kT * kT (the 4 simultaneous mu) and
+collects all g_k, the bisection on all of them gives mu* exactly as in the
+two-pass form, and p(mu*) is the Lagrange interpolant of the 4 accumulators
+when mu* lies in the bracket (else a third pass runs at mu*).
 Host code only sequences calls and moves a few scalars (bounds, degree, mu).
 """
 
@@ -92,10 +102,7 @@ def powers(pb: Problem, exponents=(-1.0, 0.5, -0.5), tol: float = 1e-10, n_max: 
     prec = pb.precision if precision is None else precision
     plan = pb.plan64 if prec == L.F64 else pb.planX
     if bounds_S is None:
-        e0, e1, th = L.bounds(pb.S, lanczos_k)
-        if th[0] <= 0:
-            raise L.ChebError(L.ERR_NOT_SPD, f"Lanczos lower Ritz value {th[0]} <= 0")
-        e0 = max(e0, 0.5 * th[0])
+        e0, e1 = L.bounds_spd(pb.S, lanczos_k)
     else:
         e0, e1 = bounds_S
     St = pb.S.with_vals(L.scale(pb.S, e0, e1))
@@ -146,64 +153,129 @@ def postprocess(pb: Problem, A: torch.Tensor, p: torch.Tensor) -> torch.Tensor:
     return F
 
 
-def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FERMI, n_max: int = 16384,
-        lanczos_k: int = 40, tol_N: float | None = None, bounds_S=None, n_S=None, bounds_H=None, n_H=None,
-        max_iter: int = 100, n_mu: int = 1, mu_stencil: float = 0.05, tol_S: float | None = None,
-        stepwise: bool = True, isqrt: str = "f64", timings: dict | None = None) -> dict:
-    """Density matrix F with Tr(F S) = N_e (see the module docstring for the steps).
+def overlap_setup(pb: Problem, tol_S: float = 1e-10, lanczos_k: int = 40, bounds_S=None, n_S=None,
+                  isqrt: str = "f64") -> dict:
+    """S^-1/2 (A) and the trace-functional matrix G: the parts of the FOE that
+    depend on the overlap only (steps 2 of the module docstring).
 
     isqrt: "f64" expands S^-1/2 in FP64; "f32ns" expands it in the problem's
-    reduced precision and applies one FP64 Newton-Schulz correction.
-    """
-    tm = {} if timings is None else timings
-    t0 = time.perf_counter()
-    tS = tol if tol_S is None else tol_S
+    reduced precision and applies one FP64 Newton-Schulz correction."""
     if isqrt == "f32ns" and pb.precision != L.F64:
-        pw = powers(pb, exponents=(-0.5,), tol=tS, bounds_S=bounds_S, n_terms=n_S, precision=pb.precision)
+        pw = powers(pb, exponents=(-0.5,), tol=tol_S, bounds_S=bounds_S, n_terms=n_S, precision=pb.precision,
+                    lanczos_k=lanczos_k)
         A = pb.zeros_out()
         L.newton_schulz_isqrt(pb.plan64, pb.S, pw["acc"][0], A, pb.zeros_out(), pb.zeros_out())
     else:
-        pw = powers(pb, exponents=(-0.5,), tol=tS, bounds_S=bounds_S, n_terms=n_S, precision=L.F64)
+        pw = powers(pb, exponents=(-0.5,), tol=tol_S, bounds_S=bounds_S, n_terms=n_S, precision=L.F64,
+                    lanczos_k=lanczos_k)
         A = pw["acc"][0]
+    G = trace_functional(pb, A)
+    return {"A": A, "G": G, "bounds_S": pw["bounds"], "n_S": pw["n_terms"]}
+
+
+def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FERMI, n_max: int = 16384,
+        lanczos_k: int = 40, tol_N: float | None = None, bounds_S=None, n_S=None, bounds_H=None, n_H=None,
+        max_iter: int = 100, form: str = "twopass", n_mu: int = 4, mu_half_kT: float = 0.02,
+        overlap: dict | None = None, tol_S: float | None = None, penalty_alpha: float = -200.0,
+        penalty_threshold: float = 1.0, penalty_widen: float = 0.05, penalty_terms: int = 512,
+        stepwise: bool = True, isqrt: str = "f64", timings: dict | None = None) -> dict:
+    """Density matrix F with Tr(F S) = N_e (see the module docstring for the steps).
+
+    form: "twopass" (moment pass, bisection, accumulation pass) or "mu4" (a
+    half-length moment pass brackets mu*, one pass accumulates n_mu mu at
+    once and collects all moments, interpolation at mu*).  overlap: the
+    result of overlap_setup for this problem's S (computed here if None).
+    The penalty check (Eq. 5) runs on the first penalty_terms Tr T_k of pass 1
+    with alpha = penalty_alpha in the scaled variable (|alpha| capped at 2/5 of
+    the terms it is expanded in, so that the penalty polynomial resolves it):
+    a failing bound is widened by penalty_widen of the interval width and pass
+    1 repeated once; a second failure raises ChebError(ERR_BOUNDS).
+    """
+    if form not in ("twopass", "mu4"):
+        raise ValueError(f"foe: unknown form {form!r}")
+    tm = {} if timings is None else timings
+    t0 = time.perf_counter()
+    tS = tol if tol_S is None else tol_S
+    ov = overlap_setup(pb, tS, lanczos_k, bounds_S, n_S, isqrt) if overlap is None else overlap
+    A, G = ov["A"], ov["G"]
     Hp = orthogonalise(pb, A)
     if bounds_H is None:
         e0, e1, _ = L.bounds(Hp, lanczos_k)
     else:
         e0, e1 = bounds_H
-    Hpt = Hp.with_vals(L.scale(Hp, e0, e1))
-    G = trace_functional(pb, A)
-    mid = 0.5 * (e0 + e1)
-    if n_H is None:
-        n, _ = L.coeffs([{"kind": kind, "mu": mid, "kT": kT}], e0, e1, tol, n_max, device=pb.device)
-    else:
-        n = n_H
-    tm["setup_s"] = time.perf_counter() - t0
-    t = torch.zeros(n, dtype=torch.float64, device=pb.device)
-    g = torch.zeros(n, dtype=torch.float64, device=pb.device)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    ev[0].record()
-    ws = L.expand(pb.planX, Hpt, n, None, [], moments=t, G=G, gmoments=g, precision=pb.precision, stepwise=stepwise)
-    ev[1].record()
     if tol_N is None:
         tol_N = 1e-9 * N_e if pb.precision == L.F64 else 1e-6 * N_e
-    res = L.mu_search(g, n, e0, e1, kind, kT, N_e, tol_N, max_iter)
-    r = L.decode_mu_result(res)
-    mu = r["mu"]
-    # pass 2 accumulates F at mu* and at the three neighbours of the 4-point
-    # stencil mu* + {-1, 1, 2} h, h = mu_stencil * kT (n_mu = 4 simultaneous mu)
-    mus = [mu] + ([mu + d * mu_stencil * kT for d in (-1.0, 1.0, 2.0)] if n_mu == 4 else [])
-    _, c = L.coeffs([{"kind": kind, "mu": m, "kT": kT} for m in mus], e0, e1, 0.0, n, device=pb.device)
-    accs = [pb.zeros_out() for _ in mus]
-    ev[2].record()
-    L.expand(pb.planX, Hpt, n, c, accs, precision=pb.precision, ws=ws, stepwise=stepwise)
-    ev[3].record()
-    p = accs[0]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    ws = None
+    penalty = []
+    for attempt in range(2):
+        Hpt = Hp.with_vals(L.scale(Hp, e0, e1))
+        if n_H is None:
+            n, _ = L.coeffs([{"kind": kind, "mu": 0.5 * (e0 + e1), "kT": kT}], e0, e1, tol, n_max, device=pb.device)
+        else:
+            n = n_H
+        m = n // 2 if form == "mu4" else n
+        tm["setup_s"] = time.perf_counter() - t0
+        t = torch.zeros(m, dtype=torch.float64, device=pb.device)
+        g = torch.zeros(m, dtype=torch.float64, device=pb.device)
+        ev[0].record()
+        ws = L.expand(pb.planX, Hpt, m, None, [], moments=t, G=G, gmoments=g, precision=pb.precision, ws=ws,
+                      stepwise=stepwise)
+        ev[1].record()
+        npen = min(m, penalty_terms)
+        alpha = -min(abs(penalty_alpha), 0.4 * npen)
+        verdict, value = L.penalty_check(t, npen, alpha, penalty_threshold)
+        penalty.append((verdict, value, (e0, e1)))
+        if verdict == 0:
+            break
+        if attempt == 1:
+            raise L.ChebError(L.ERR_BOUNDS, f"penalty check (Eq. 5) failed twice: trace {value:g} on [{e0}, {e1}]")
+        w = penalty_widen * (e1 - e0)
+        if verdict in (-1, 2):
+            e0 -= w
+        if verdict in (1, 2):
+            e1 += w
+    passes = 1
+    if form == "twopass":
+        res = L.mu_search(g, n, e0, e1, kind, kT, N_e, tol_N, max_iter)
+        r = L.decode_mu_result(res)
+        mu = r["mu"]
+        _, c = L.coeffs([{"kind": kind, "mu": mu, "kT": kT}], e0, e1, 0.0, n, device=pb.device)
+        p = pb.zeros_out()
+        ev[2].record()
+        L.expand(pb.planX, Hpt, n, c, [p], precision=pb.precision, ws=ws, stepwise=stepwise)
+        ev[3].record()
+        passes = 2
+        mus, gm = [mu], g
+        r_half = None
+    else:
+        r_half = L.decode_mu_result(L.mu_search(g, m, e0, e1, kind, kT, N_e, tol_N, max_iter))
+        mus = L.mu_nodes(r_half["mu"], mu_half_kT * kT, n_mu)
+        _, c = L.coeffs([{"kind": kind, "mu": x, "kT": kT} for x in mus], e0, e1, 0.0, n, device=pb.device)
+        accs = [pb.zeros_out() for _ in mus]
+        gm = torch.zeros(n, dtype=torch.float64, device=pb.device)
+        ev[2].record()
+        L.expand(pb.planX, Hpt, n, c, accs, G=G, gmoments=gm, precision=pb.precision, ws=ws, stepwise=stepwise)
+        ev[3].record()
+        passes = 2
+        r = L.decode_mu_result(L.mu_search(gm, n, e0, e1, kind, kT, N_e, tol_N, max_iter))
+        mu = r["mu"]
+        p = pb.zeros_out()
+        ev[4].record()
+        if abs(mu - r_half["mu"]) <= mu_half_kT * kT:
+            L.lincomb(L.lagrange_weights(mus, mu), accs, p)
+        else:
+            _, c3 = L.coeffs([{"kind": kind, "mu": mu, "kT": kT}], e0, e1, 0.0, n, device=pb.device)
+            L.expand(pb.planX, Hpt, n, c3, [p], precision=pb.precision, ws=ws, stepwise=stepwise)
+            passes = 3
+        ev[5].record()
     F = postprocess(pb, A, p)
     trFS = L.trace(pb.P_out.with_vals(F), pb.S)
     tm["events"] = ev
-    return {"F": F, "p": p, "acc_mu": accs, "mus": mus, "A": A, "Hp": Hp, "G": G, "mu": mu, "mu_result": r,
-            "moments": t, "gmoments": g, "n_terms": n, "bounds_H": (e0, e1), "bounds_S": pw["bounds"],
-            "n_S": pw["n_terms"], "trace_FS": trFS}
+    tm["form"] = form
+    return {"F": F, "p": p, "mus": mus, "A": A, "Hp": Hp, "G": G, "mu": mu, "mu_result": r, "mu_half": r_half,
+            "moments": t, "gmoments": gm, "n_terms": n, "n_pass1": m, "passes": passes, "bounds_H": (e0, e1),
+            "bounds_S": ov["bounds_S"], "n_S": ov["n_S"], "trace_FS": trFS, "penalty": penalty}
 
 
 def selected_eigenvalues(pb: Problem, kT: float, intervals=(), levels=(), tol: float = 1e-9, n_max: int = 16384,

@@ -35,9 +35,22 @@ def test_batched_sizes_are_seeded_and_in_range():
 
 
 def test_step_bytes_counts_each_stream_once():
-    # T_k, T_{k-1} read and T_{k+1} written, the operator, accumulators read and written, G read
-    assert bench.step_bytes(10, 4, 4, 0, False) == 10 * 16 * 4 * 3 + 4 * 16 * 4
-    assert bench.step_bytes(10, 4, 8, 2, True) == 10 * 16 * 8 * 3 + 4 * 16 * 8 + 10 * 16 * 8 * 2 * 2 + 10 * 16 * 8
+    # T_k, T_{k-1} read and T_{k+1} written (FP32), the operator (FP32), each
+    # accumulator read and written (8 bytes per element), G read (8 bytes)
+    assert bench.col_step_bytes(10, 4, 0, False) == 10 * 16 * 4 * 3 + 4 * 16 * 4
+    assert bench.col_step_bytes(10, 4, 2, True) == 10 * 16 * 4 * 3 + 4 * 16 * 4 + 10 * 16 * 8 * 2 * 2 + 10 * 16 * 8
+
+
+def test_solve_step_equivalents():
+    # a half-length moment pass, a full accumulation pass, four P_out products
+    assert bench.solve_step_equivalents(100, 50, 30, 10) == 48 + 98 + 12
+    assert bench.solve_step_equivalents(100, 100, 10, 10) == 98 + 98 + 4
+
+
+def test_default_workload_is_the_mixed_40k_solve_with_four_mu():
+    cfg = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]
+    assert cfg["n_atoms"] == 10000 and cfg["precision"] == "f32" and cfg["kT"] == 0.005
+    assert cfg["n_mu"] == 4 and cfg["form"] == "mu4"
 
 
 def test_oracle_threads_follow_omp_setting(monkeypatch):

@@ -504,3 +504,73 @@ def test_newton_schulz_isqrt_squares_the_error():
         assert e1 < 3 * e0 ** 2
     Z1 = ref.newton_schulz_isqrt(S, _bsr_from_dense(Z, P.row_ptr, P.col_idx), P).dense()
     assert ref.rel_frobenius(Z1, Z) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# column-sampled expansion, erfc occupations, penalty side
+# --------------------------------------------------------------------------
+
+def test_column_expand_matches_masked_dense_brute_force():
+    # the C column recursion against dense matrices masked after each product
+    s, S, H, P_H, P_out = _small_system(n_atoms=40, r_c=3.0, r_out=4.5, seed=17)
+    Hd = H.dense()
+    nat = P_out.nbr
+    mask_blk = np.zeros((nat, nat), bool)
+    rows = np.repeat(np.arange(nat), np.diff(P_out.row_ptr))
+    mask_blk[rows, P_out.col_idx] = True
+    mask = np.kron(mask_blk, np.ones((4, 4), bool))
+    w = sla.eigvalsh(Hd)
+    emin, emax = w[0] - 0.1, w[-1] + 0.1
+    Ht = ref.scale(H, emin, emax)
+    Htd = Ht.dense()
+    n = 35
+    c = np.random.default_rng(5).normal(size=(2, n)) / (1 + np.arange(n))
+    Ts = [np.eye(4 * nat) * mask, Htd * mask]
+    for k in range(1, n - 1):
+        Ts.append(2.0 * (Htd @ Ts[-1]) * mask - Ts[-2])
+    cols = [0, 3, 17, 39]
+    got = ref.column_expand(Ht, P_out, cols, c)
+    for j in range(2):
+        want = 0.5 * c[j, 0] * Ts[0] + sum(c[j, k] * Ts[k] for k in range(1, n))
+        for ci, J in enumerate(cols):
+            I = P_out.col_idx[P_out.row_ptr[J]:P_out.row_ptr[J + 1]]
+            wb = np.stack([want[4 * i:4 * i + 4, 4 * J:4 * J + 4] for i in I])
+            assert np.max(np.abs(got[j][ci] - wb)) < 1e-11
+
+
+def test_erfc_occupations_count_brute_force_levels():
+    # Eq. 9 with beta = 1/kT: on a diagonal operator the re-summed count
+    # sum_k c_k(mu) g_k (g_k = sum_i T_k(x~_i)) equals sum_i erfc((e_i - mu)/kT)/2
+    # computed level by level with the standard library's erfc
+    import math
+    rng = np.random.default_rng(23)
+    eps = np.sort(rng.uniform(-1.0, 1.5, 60))
+    emin, emax = -1.2, 1.7
+    s_, t_ = ref.sigma_tau(emin, emax)
+    x = s_ * (eps - t_)
+    n = 1024
+    g = np.array([np.sum(np.cos(k * np.arccos(x))) for k in range(n)])
+    kT, mu = 0.04, 0.3
+    got = ref.electron_count(g, ref.Func(ref.KIND_ERFC, mu=mu, kT=kT), emin, emax)
+    want = sum(0.5 * math.erfc((e - mu) / kT) for e in eps)
+    assert abs(got - want) < 1e-9 * len(eps)
+    # occupied below mu, empty above, one half at mu, and the two tails of one
+    # width add to one (erfc(-y) = 2 - erfc(y))
+    f = ref.Func(ref.KIND_ERFC, mu=mu, kT=kT)
+    assert f(mu - 5 * kT) > 1 - 1e-10 and f(mu + 5 * kT) < 1e-10 and f(mu) == 0.5
+    for d in (0.3 * kT, kT, 2.5 * kT):
+        assert abs(f(mu - d) + f(mu + d) - 1.0) < 1e-15
+    assert abs(f(mu + kT) - 0.5 * math.erfc(1.0)) < 1e-15
+
+
+def test_penalty_side_shows_in_the_sign_pattern_of_the_moments():
+    # a level below -1 makes T_k(x) = (-1)^k cosh(k acosh|x|) dominate the
+    # moments (alternating signs); a level above +1 gives one sign
+    s, S, H, P_H, P_out = _small_system(n_atoms=20, r_c=4.0, r_out=6.0, seed=10)
+    w = np.linalg.eigvalsh(S.dense())
+    wd = w[-1] - w[0]
+    n = 120
+    for emin, emax, side in [(w[0] + 0.1 * wd, w[-1] + 0.05 * wd, -1), (w[0] - 0.05 * wd, w[-1] - 0.1 * wd, 1)]:
+        ex = ref.chebyshev_expand(ref.scale(S, emin, emax), P_out, np.zeros((1, n)))
+        assert abs(ref.penalty_trace(ex.t, -40.0, emin, emax)) >= 1.0
+        assert (-1 if ex.t[-1] * ex.t[-2] < 0 else 1) == side
