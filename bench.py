@@ -428,7 +428,8 @@ def run_cheb(args, rank: int, world: int, local: int):
         print(json.dumps(res), flush=True)
 
 
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (the FMA-loop probe measured 1.19)
+# GB300 FP64: 304 DFMA lanes per cycle (152 SMs x 2, ncu peak_sustained) x 2 flops x 2070 MHz
+FP64_NOMINAL_TFLOPS = 1.26
 
 
 def run_powers(args, rank: int, world: int, local: int):
@@ -502,7 +503,8 @@ def run_powers(args, rank: int, world: int, local: int):
                    "triples": triples, "l2": "inputs larger than L2 (no flush)"},
         "roofline": {"bound": "alu", "achieved": round(tflops, 4), "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                      "frac": round(tflops / FP64_NOMINAL_TFLOPS, 4), "traffic": None,
-                     "kernel": "k_step<double,2,8>", "peak_source": "GB300 nominal FP64 (measured 1.19)"},
+                     "kernel": "k_step<double,2,8>",
+                     "peak_source": "FP64 unit count: 304 DFMA lanes per cycle x 2 flops x 2070 MHz"},
         "e2e": {"value": round(job_throughput(args.e2e_steps, world, te_ms), 4), "unit": UNIT,
                 "h2d_bytes_per_step": int(h_S.numel() * 8), "d2h_bytes_per_step": int(sum(h.numel() for h in h_out) * 8)},
         "gpu_launches": int(launches), "clocks": clocks,

@@ -275,8 +275,9 @@ __global__ void __launch_bounds__(NW * 32, 1) k_colstep(const ColArgs a) {
     }
     __syncthreads();
 
-    double tpart[3] = {0.0, 0.0, 0.0};         // Tr T of terms k-1, k, k+1
-    float gh[3] = {0.f, 0.f, 0.f}, gl[3] = {0.f, 0.f, 0.f};  // <T, G> of those terms, double-float
+    // Tr T and <T, G> of terms k-1, k, k+1, double-float partial sums
+    float th[3] = {0.f, 0.f, 0.f}, tl[3] = {0.f, 0.f, 0.f};
+    float gh[3] = {0.f, 0.f, 0.f}, gl[3] = {0.f, 0.f, 0.f};
     const int q = lane % P, kg = lane / P;
     const int i0 = kg * EPL;
     // 16-byte chunk c of a staged block of K-group kg sits at chunk c ^ skw, so
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_colstep(const ColArgs a) {
             if (hf && ((q >> 1) != 0 || ((q & 1) && cb == ca))) p = -1;
         };
         int r = r0;
-        uint32_t rw = a.rows[r], rwn = r + 1 < r1 ? a.rows[r + 1] : 0u;
+        uint32_t rw = a.rows[r], rwn = r + 1 < r1 ? a.rows[r + 1] : 0u, rwm = r + 2 < r1 ? a.rows[r + 2] : 0u;
         int s = (int)(rw & SM), cl = (int)(rw >> COL_ROW_SHIFT);
         bool half = (rw >> COL_SLOT_BITS) & 1u;
         int col, pos, coln = 0, posn = -1;
@@ -490,7 +491,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_colstep(const ColArgs a) {
 #pragma unroll
                                 for (int j = 0; j < EPL; ++j) {
                                     ff_add_prod(gh[t3], gl[t3], tv[t3][j], gv[2 * j], gv[2 * j + 1]);
-                                    if (diag && (i0 + j) % 5 == 0) tpart[t3] += (double)tv[t3][j];  // elements 0, 5, 10, 15
+                                    // diagonal elements 0, 5, 10, 15 of a diagonal block
+                                    if (diag && (i0 + j) % 5 == 0) ff_add_prod(th[t3], tl[t3], tv[t3][j], 1.f, 0.f);
                                 }
                             }
                     }
@@ -499,8 +501,11 @@ __global__ void __launch_bounds__(NW * 32, 1) k_colstep(const ColArgs a) {
                 for (int i = 0; i < 16; ++i) acc[i] = 0.f;
                 // the next row of this warp
                 if (++r < r1) {
+                    // row words are fetched two rows ahead, so that the next
+                    // row's output position is known without waiting
                     rw = rwn;
-                    rwn = r + 1 < r1 ? a.rows[r + 1] : 0u;
+                    rwn = rwm;
+                    rwm = r + 2 < r1 ? a.rows[r + 2] : 0u;
                     s = (int)(rw & SM);
                     cl = (int)(rw >> COL_ROW_SHIFT);
                     half = (rw >> COL_SLOT_BITS) & 1u;
@@ -517,8 +522,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_colstep(const ColArgs a) {
     // 4. the moment partials of the panel
     if (a.grp && (a.mom || a.gmom)) {
         auto on = [&](int t3) { return (a.grp >> (2 - t3)) & 1; };
-        Moments<6> mm{{tpart[0], tpart[1], tpart[2], (double)gh[0] + (double)gl[0], (double)gh[1] + (double)gl[1],
-                       (double)gh[2] + (double)gl[2]},
+        Moments<6> mm{{(double)th[0] + (double)tl[0], (double)th[1] + (double)tl[1], (double)th[2] + (double)tl[2],
+                       (double)gh[0] + (double)gl[0], (double)gh[1] + (double)gl[1], (double)gh[2] + (double)gl[2]},
                       {a.mom && on(0) ? a.mom - 2 : nullptr, a.mom && on(1) ? a.mom - 1 : nullptr,
                        a.mom && on(2) ? a.mom : nullptr, a.gmom && on(0) ? a.gmom - 2 : nullptr,
                        a.gmom && on(1) ? a.gmom - 1 : nullptr, a.gmom && on(2) ? a.gmom : nullptr}};
@@ -758,15 +763,26 @@ static void col_fill(const ColLists &c, const std::vector<int64_t> &rp, const st
                     const int32_t sl = slot_of[lci[e]];
                     cls[sl % rq].push_back(((uint32_t)e << COL_SLOT_BITS) | (uint32_t)sl);
                 }
+            // position p of a chunk (8 K-groups x 2 entries) takes slot residue
+            // (p ^ (p >> 3)) mod 2, so that the two K-groups of a quarter warp
+            // differ in it both for the entries e = 0, 1 of a full row and for
+            // the pair (p, p + 8) that a half row's lane quads read together;
+            // when one residue runs out the other fills in
             std::vector<uint32_t> &r = rent[u];
             std::vector<size_t> at(rq, 0);
-            for (bool more = true; more;) {
-                more = false;
-                for (int k = 0; k < rq; ++k)
-                    if (at[k] < cls[k].size()) {
-                        r.push_back(cls[k][at[k]++]);
-                        more = true;
-                    }
+            size_t left = 0;
+            for (auto &v : cls) left += v.size();
+            for (size_t pos = 0; left > 0; ++pos) {
+                const int p = (int)(pos % (size_t)CW);
+                int k = ((p ^ (p >> 3)) & 1) % rq;
+                if (at[k] >= cls[k].size())
+                    for (int kk = 0; kk < rq; ++kk)
+                        if (at[kk] < cls[kk].size()) {
+                            k = kk;
+                            break;
+                        }
+                r.push_back(cls[k][at[k]++]);
+                --left;
             }
             mr = std::max(mr, (int32_t)r.size());
             const size_t padded = std::max<size_t>(1, (r.size() + CW - 1) / CW) * CW;
