@@ -63,6 +63,11 @@ WORKLOADS = {
     # profiler capture of a whole solve short.
     "foe_mixed_12k_kT05": dict(n_atoms=3000, r_c=10.0, r_buf=4.0, kT=0.05, N_e=6000.0, tol=1e-7, tol_S=1e-10,
                                precision="f32", n_mu=4, form="mu4"),
+    # The smearing chosen on the fly on the 12,000-row system: two-pass solves
+    # from kT = 0.04 Ha, halved until E = Tr(K H) and E' of the same polynomials
+    # at 1.25 kT differ by at most dE_tol (0.2 Ha, 6.7e-5 Ha per atom).
+    "foe_mixed_12k_autokT": dict(n_atoms=3000, r_c=10.0, r_buf=4.0, kT=0.04, N_e=6000.0, tol=1e-7, tol_S=1e-10,
+                                 precision="f32", n_mu=1, form="autokT", dE_tol=0.2, widen=1.25, shrink=0.5),
     # The plain FP64 density matrix: 200 atoms x 4, 8 bohr cutoff, kT = 0.01, N_e = 400.
     "foe_fp64_800": dict(n_atoms=200, r_c=8.0, r_buf=4.0, kT=0.01, N_e=400.0, tol=1e-10, tol_S=1e-10,
                          precision="f64", n_mu=1, form="twopass"),
@@ -274,6 +279,10 @@ def run_cheb(args, rank: int, world: int, local: int):
             e0, e1, _ = cg.bounds(Hp, 40)
             prepared = (A, Hp.with_vals(cg.scale(Hp, e0, e1)), (e0, e1), G)
             return learned.foe_learned(pb, prop, prepared=prepared, timings=timings, **kw)
+    elif form == "autokT":
+        def solve_once(timings=None):
+            return solve.foe_auto_kT(pb, cfg["kT"], cfg["N_e"], cfg["dE_tol"], cfg["widen"], cfg["shrink"],
+                                     tol=cfg["tol"], overlap=ov, timings=timings)
     else:
         kw = dict(kT=cfg["kT"], N_e=cfg["N_e"], tol=cfg["tol"], n_mu=cfg["n_mu"], form=form)
 
@@ -356,9 +365,12 @@ def run_cheb(args, rank: int, world: int, local: int):
         bytes_pass = [col_step_bytes(nnz_out, nnz_H, 0, True), col_step_bytes(nnz_out, nnz_H, cfg["n_mu"], True)]
         p_ms = [statistics.mean(ev[0].elapsed_time(ev[1]) for ev in pass_ev),
                 statistics.mean(ev[2].elapsed_time(ev[3]) for ev in pass_ev)]
-    elif prec == cg.F32 and form == "twopass":
+    elif prec == cg.F32 and form in ("twopass", "autokT"):
+        # (the smearing loop: the passes of its accepted round, whose second
+        # pass also collects the energy moments)
         launches_pass = [n_terms - 2, n_terms - 2]
-        bytes_pass = [col_step_bytes(nnz_out, nnz_H, 0, True), col_step_bytes(nnz_out, nnz_H, 1, False)]
+        bytes_pass = [col_step_bytes(nnz_out, nnz_H, 0, True),
+                      col_step_bytes(nnz_out, nnz_H, 1, form == "autokT")]
         p_ms = [statistics.mean(ev[0].elapsed_time(ev[1]) for ev in pass_ev),
                 statistics.mean(ev[2].elapsed_time(ev[3]) for ev in pass_ev)]
     else:
@@ -418,10 +430,13 @@ def run_cheb(args, rank: int, world: int, local: int):
                   "passes": [o["passes"] for o in outs],
                   **({"mu_half_minus_mu_kT": (out["mu_half"]["mu"] - out["mu"]) / cfg["kT"]}
                      if form == "mu4" else {}),
+                  **({"rounds_kT_n_E_Eprime_ok": out["rounds"], "dE_tol": cfg["dE_tol"]}
+                     if form == "autokT" else {}),
                   **({"mu_hat": out["mu_hat"], "half_kT": out["half"] / cfg["kT"]} if form == "learned" else {})},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(sysm, cfg, n_terms, out.get("n_pass1", n_terms))
+        res["cpu_baseline"] = cpu_baseline(sysm, cfg, n_terms, out.get("n_pass1", n_terms),
+                                           [r[1] for r in out.get("rounds", [])[:-1]])
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
@@ -648,9 +663,12 @@ def solve_step_equivalents(n_terms: int, n_pass1: int, nnz_out: int, nnz_H: int)
     return (n_pass1 - 2) + (n_terms - 2) + 4 * nnz_out / nnz_H
 
 
-def cpu_baseline(sysm, cfg, n_terms, n_pass1) -> dict:
+def cpu_baseline(sysm, cfg, n_terms, n_pass1, earlier_rounds=()) -> dict:
+    """earlier_rounds: term counts of two-pass solves that preceded the accepted
+    one (the smearing loop), each counted as a whole solve."""
     t_step, nnz_out = oracle_sample(sysm, cfg, 1)
     eq = solve_step_equivalents(n_terms, n_pass1, nnz_out, sysm.nnzb)
+    eq += sum(solve_step_equivalents(n, n, nnz_out, sysm.nnzb) for n in earlier_rounds)
     return {"value": 1.0 / (t_step * eq), "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
             "extrapolated": True,
             "sample": f"1 FP64 oracle recursion step of the same system timed ({t_step:.2f}s), extrapolated by "

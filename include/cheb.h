@@ -206,6 +206,19 @@ int cheb_bounds(const cheb_bsr *M, int32_t k, const double *v0, double margin_fr
                 double *emin, double *emax, double *theta, void *ws, size_t ws_bytes,
                 void *stream);
 
+/* Warm start (Sec. "Determination of the eigenvalue bounds and polynomial
+ * degree": in a self-consistent loop the bounds of the previous step are a
+ * good guess, checked on the fly by the penalty trace).  As cheb_bounds, with
+ * the result the hull of warm = [lo, hi] (host double[2], lo < hi) and the
+ * Lanczos interval: Ritz values always lie within the spectrum, so a warm
+ * bound that falls inside the Lanczos interval is widened to it, and a warm
+ * interval that already contains it is kept (few Lanczos steps suffice).
+ * Host-returning; same workspace as cheb_bounds.  Errors: as cheb_bounds, and
+ * CHEB_ERR_INVALID for a NULL or empty warm interval. */
+int cheb_bounds_warm(const cheb_bsr *M, int32_t k, const double *v0, double margin_frac,
+                     const double *warm, double *emin, double *emax, double *theta, void *ws,
+                     size_t ws_bytes, void *stream);
+
 /* Bounds of an SPD matrix for the matrix powers (Sec. "Matrix powers"): as
  * cheb_bounds, then CHEB_ERR_NOT_SPD if the lowest Ritz value is <= 0, and the
  * lower bound raised to at least half the lowest Ritz value (the paper's
@@ -243,9 +256,12 @@ int cheb_coeffs(const cheb_func *funcs, int32_t n_f, double emin, double emax, d
  *   coeffs: device double[n_f][coeff_stride]; acc: host array of n_f device
  *   pointers, each double[nnzb(P_out)*16] in BCSR order on P_out (overwritten);
  *   moments, gmoments: device double[n_terms] or NULL; G: device double on
- *   P_out or NULL.  precision: CHEB_F64 (T_k and products in FP64) or CHEB_F32
+ *   P_out or NULL.  precision: CHEB_F64 (T_k and products in FP64), CHEB_F32
  *   (Mt rounded to FP32, T_k stored and multiplied in FP32, accumulators and
- *   moments in FP64).  Results are bitwise reproducible run to run.
+ *   moments in FP64) or CHEB_BF16 with a CHEB_BF16 plan (as CHEB_F32, with Mt
+ *   and every stored T_k rounded to bfloat16, round to nearest even: bfloat16
+ *   block products summed in FP32).  Results are bitwise reproducible run to
+ *   run.
  *
  * cheb_expand runs the whole expansion in one kernel launch: every thread
  * block owns a panel of block columns (columns are independent under Eq. 3)
@@ -351,6 +367,15 @@ int cheb_trace(const cheb_bsr *A, const cheb_bsr *B, double *out, void *ws, size
  */
 int cheb_penalty_trace(const double *moments, int32_t n_terms, double alpha, double *out,
                        void *ws, size_t ws_bytes, void *stream);
+
+/* A re-summed trace: out (device double[1]) = coeffs[0]/2 moments[0] +
+ * sum_{k>=1} coeffs[k] moments[k] (device arrays of n_terms).  With the
+ * moments <T_k, G_H> of the energy functional and the coefficients of an
+ * occupation function it is E = Tr(K H) for that function without new
+ * products -- the energy comparison that chooses beta (Sec. "Fermi Operator
+ * Expansion": K and K' differ only in their coefficients).  Asynchronous. */
+int cheb_series_value(const double *coeffs, const double *moments, int32_t n_terms, double *out,
+                      void *stream);
 
 /* The same trace as a decision on the solve path (host-returning): *value
  * (host, may be NULL) = the penalty trace of the first n_terms (>= 3)
@@ -469,6 +494,11 @@ int cheb_lagrange_weights(const double *nodes, int32_t n, double x, double *weig
  *     the batch into *loss (device double, may be NULL); dout = dL/dout.
  *   backward: grad (device float[param_count]) of sum(dout * out); ws device
  *     float[batch*256].
+ *   init: Xavier-uniform weights W ~ U(-a, a), a = sqrt(6/(fan_in + fan_out)),
+ *     biases 0, into theta (device float[param_count]).  The uniform of
+ *     parameter i is u = (top 24 bits of splitmix64((seed * 0xD1B54A32D192ED03)
+ *     xor i) + 1/2) / 2^24 (splitmix64: Steele, Lea and Flood, 2014); the
+ *     weight a (2u - 1) is formed in FP64 and rounded once to FP32.
  *   adam: one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step t >= 1).
  *   features: the 35 inputs from t_k = Tr T_k (device double[32]): t_k/n_rows,
  *     emin/10, emax/10, N_e/n_rows -> device float[35].
@@ -476,6 +506,7 @@ int cheb_lagrange_weights(const double *nodes, int32_t n, double x, double *weig
  * (reproducible).
  */
 int cheb_mlp_param_count(void);
+int cheb_mlp_init(float *theta, uint64_t seed, void *stream);
 int cheb_mlp_forward(const float *theta, const float *X, int32_t batch, float *act, float *out,
                      void *stream);
 int cheb_mlp_loss(const float *out, const float *xstar, const float *scale, int32_t batch,

@@ -27,6 +27,38 @@ SHAPES = [("W1", (N_H, N_IN)), ("b1", (N_H,)), ("W2", (N_H, N_H)), ("b2", (N_H,)
 N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
 
 
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 output for state x (Steele, Lea and Flood, "Fast splittable
+    pseudorandom number generators", OOPSLA 2014): add the golden-ratio
+    increment, then two xor-shift-multiply rounds and a final xor-shift."""
+    x = np.asarray(x, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = x + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def xavier_init(seed: int) -> np.ndarray:
+    """Xavier-uniform weights W ~ U(-a, a), a = sqrt(6 / (fan_in + fan_out)),
+    zero biases, as FP32.  Parameter i draws u = (top 24 bits of
+    splitmix64((seed * 0xD1B54A32D192ED03) xor i) + 1/2) / 2^24 and takes
+    a (2u - 1) in float64, rounded once to float32."""
+    i = np.arange(N_PARAMS, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        ctr = (np.uint64(seed & 0xFFFFFFFFFFFFFFFF) * np.uint64(0xD1B54A32D192ED03)) ^ i
+    u = ((splitmix64(ctr) >> np.uint64(40)).astype(np.float64) + 0.5) / 16777216.0
+    theta = np.zeros(N_PARAMS, dtype=np.float64)
+    o = 0
+    for name, shp in SHAPES:
+        n = int(np.prod(shp))
+        if name.startswith("W"):
+            a = np.sqrt(6.0 / (shp[0] + shp[1]))
+            theta[o:o + n] = a * (2.0 * u[o:o + n] - 1.0)
+        o += n
+    return theta.astype(np.float32)
+
+
 def unpack(theta: np.ndarray) -> dict:
     out, o = {}, 0
     for name, shp in SHAPES:

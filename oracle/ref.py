@@ -571,6 +571,16 @@ def electron_count(g: np.ndarray, f: Func, emin: float, emax: float) -> float:
     return 0.5 * c[0] * g[0] + float(np.dot(c[1:], g[1:]))
 
 
+def energy(e: np.ndarray, f: Func, emin: float, emax: float) -> float:
+    """E = Tr(K H) = c_0/2 e_0 + sum_k c_k e_k, with the energy moments
+    e_k = <T_k, G_H> (G_H = trace_functional_matrix(A, H, P_out)).  The energy
+    is linear in the coefficients like the electron count, so the energy of a
+    second kernel K' of the same polynomials (another smearing, another mu) is
+    a re-sum as well (Sec. "Fermi Operator Expansion", the choice of beta)."""
+    c = cheb_coeffs(f, len(e), emin, emax)
+    return 0.5 * c[0] * e[0] + float(np.dot(c[1:], e[1:]))
+
+
 @dataclasses.dataclass
 class MuSearch:
     mu: float

@@ -30,10 +30,11 @@ EXPORTS = [
     "cheb_coeffs_workspace_size", "cheb_coeffs", "cheb_expand_workspace_size", "cheb_expand",
     "cheb_expand_stepwise_workspace_size", "cheb_expand_stepwise", "cheb_plan_create_batched",
     "cheb_plan_resident_info", "cheb_expand_batched", "cheb_block_diag", "cheb_lincomb", "cheb_mlp_param_count",
-    "cheb_mlp_forward", "cheb_mlp_loss", "cheb_mlp_backward", "cheb_mlp_adam", "cheb_mlp_features",
+    "cheb_mlp_init", "cheb_mlp_forward", "cheb_mlp_loss", "cheb_mlp_backward", "cheb_mlp_adam", "cheb_mlp_features",
     "cheb_masked_product", "cheb_transpose", "cheb_restrict", "cheb_trace_workspace_size", "cheb_trace",
     "cheb_penalty_trace", "cheb_mu_search", "cheb_mu_search_noalloc", "cheb_newton_schulz", "cheb_newton_schulz_isqrt",
     "cheb_plan_col_info", "cheb_penalty_check", "cheb_mu_nodes", "cheb_lagrange_weights", "cheb_bounds_spd",
+    "cheb_series_value", "cheb_bounds_warm",
 ]
 
 
@@ -94,12 +95,15 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
         "cheb_plan_col_info": ([p, P(i64), P(i32), P(i64)], i32),
         "cheb_penalty_check": ([p, i32, dbl, dbl, P(dbl), P(i32), p, sz, p], i32),
         "cheb_mu_nodes": ([dbl, dbl, i32, P(dbl)], i32),
+        "cheb_series_value": ([p, p, i32, p, p], i32),
+        "cheb_bounds_warm": ([P(CBsr), i32, p, dbl, P(dbl), P(dbl), P(dbl), P(dbl), p, ctypes.c_size_t, p], i32),
         "cheb_lagrange_weights": ([P(dbl), i32, dbl, P(dbl)], i32),
         "cheb_bounds_spd": ([P(CBsr), i32, p, dbl, P(dbl), P(dbl), p, sz, p], i32),
         "cheb_expand_batched": ([p, P(CBsr), i32, p, p, p, i32, i32, P(p), p, p, p, i32, i32, p, sz, p], i32),
         "cheb_block_diag": ([i32, P(CBsr), p, p, p, i32, p], i32),
         "cheb_lincomb": ([i32, P(dbl), P(p), i64, p, p], i32),
         "cheb_mlp_param_count": ([], i32),
+        "cheb_mlp_init": ([p, ctypes.c_uint64, p], i32),
         "cheb_mlp_forward": ([p, p, i32, p, p, p], i32),
         "cheb_mlp_loss": ([p, p, p, i32, p, p, p], i32),
         "cheb_mlp_backward": ([p, p, i32, p, p, p, p, p], i32),
@@ -270,6 +274,22 @@ def bounds(M: Bsr, k: int = 40, v0: torch.Tensor | None = None, margin_frac: flo
     cb = M.c()
     _check(lib.cheb_bounds(ctypes.byref(cb), k, _ptr(v0), margin_frac, ctypes.byref(lo), ctypes.byref(hi), th,
                            ctypes.c_void_p(_aligned(ws)), nb.value, _stream(stream)))
+    return lo.value, hi.value, (th[0], th[1])
+
+
+def bounds_warm(M: Bsr, warm: tuple[float, float], k: int = 8, v0: torch.Tensor | None = None,
+                margin_frac: float = 0.01, stream=None) -> tuple[float, float, tuple[float, float]]:
+    """cheb_bounds_warm: the hull of the warm interval and k Lanczos steps' interval."""
+    lib = load()
+    nb = ctypes.c_size_t(0)
+    _check(lib.cheb_bounds_workspace_size(M.nbr, k, ctypes.byref(nb)))
+    ws = _ws(nb.value, M.vals.device)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    th = (ctypes.c_double * 2)()
+    w = (ctypes.c_double * 2)(float(warm[0]), float(warm[1]))
+    cb = M.c()
+    _check(lib.cheb_bounds_warm(ctypes.byref(cb), k, _ptr(v0), margin_frac, w, ctypes.byref(lo), ctypes.byref(hi),
+                                th, ctypes.c_void_p(_aligned(ws)), nb.value, _stream(stream)))
     return lo.value, hi.value, (th[0], th[1])
 
 
@@ -454,6 +474,13 @@ def penalty_check(moments: torch.Tensor, n_terms: int, alpha: float, threshold: 
     return d.value, v.value
 
 
+def series_value(coeffs: torch.Tensor, moments: torch.Tensor, n_terms: int, stream=None) -> torch.Tensor:
+    """cheb_series_value: device scalar c_0/2 t_0 + sum_k c_k t_k."""
+    out = torch.empty(1, dtype=torch.float64, device=moments.device)
+    _check(load().cheb_series_value(_ptr(coeffs), _ptr(moments), n_terms, _ptr(out), _stream(stream)))
+    return out
+
+
 def mu_nodes(center: float, half: float, n: int) -> list[float]:
     """cheb_mu_nodes: Chebyshev points of the bracket [center - half, center + half]."""
     out = (ctypes.c_double * n)()
@@ -581,6 +608,13 @@ def mlp_backward(theta, X, act, dout, grad, ws, stream=None):
     _check(load().cheb_mlp_backward(_ptr(theta), _ptr(X), X.shape[0], _ptr(act), _ptr(dout), _ptr(grad), _ptr(ws),
                                     _stream(stream)))
     return grad
+
+
+def mlp_init(seed: int, device, stream=None) -> torch.Tensor:
+    """cheb_mlp_init: Xavier-uniform parameters (zero biases) from a seeded counter-based stream."""
+    theta = torch.empty(mlp_param_count(), dtype=torch.float32, device=device)
+    _check(load().cheb_mlp_init(_ptr(theta), ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), _stream(stream)))
+    return theta
 
 
 def mlp_adam(theta, grad, m, v, t: int, lr: float, stream=None):

@@ -463,3 +463,10 @@ extern "C" int cheb_bounds_spd(const cheb_bsr *S, int32_t k, const double *v0, d
     if (*emin < 0.5 * th[0]) *emin = 0.5 * th[0];
     return CHEB_OK;
 }
+
+extern "C" int cheb_series_value(const double *coeffs, const double *moments, int32_t n_terms, double *out,
+                                 void *stream) {
+    if (!coeffs || !moments || !out || n_terms < 1) return fail(CHEB_ERR_INVALID, "cheb_series_value: bad arguments");
+    k_dot_terms<256><<<1, 256, 0, as_stream(stream)>>>(coeffs, moments, n_terms, out);
+    return check_launch("k_dot_terms");
+}

@@ -269,3 +269,15 @@ extern "C" int cheb_bounds(const cheb_bsr *M, int32_t k, const double *v0, doubl
     }
     return CHEB_OK;
 }
+
+extern "C" int cheb_bounds_warm(const cheb_bsr *M, int32_t k, const double *v0, double margin_frac,
+                                const double *warm, double *emin, double *emax, double *theta, void *ws,
+                                size_t ws_bytes, void *stream) {
+    if (!warm || !(warm[0] < warm[1])) return fail(CHEB_ERR_INVALID, "cheb_bounds_warm: warm interval needs lo < hi");
+    CHEB_TRY(cheb_bounds(M, k, v0, margin_frac, emin, emax, theta, ws, ws_bytes, stream));
+    // Ritz values lie inside the spectrum: a warm interval that misses the
+    // Lanczos interval is provably too narrow there and is extended to it
+    *emin = std::fmin(*emin, warm[0]);
+    *emax = std::fmax(*emax, warm[1]);
+    return CHEB_OK;
+}

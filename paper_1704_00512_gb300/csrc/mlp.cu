@@ -109,11 +109,47 @@ __global__ void k_features(const double *t, int64_t n_rows, double emin, double 
 
 inline unsigned nb(int64_t n, int t = 128) { return (unsigned)((n + t - 1) / t); }
 
+// Xavier-uniform initialisation: W ~ U(-a, a) with a = sqrt(6 / (fan_in +
+// fan_out)) per layer, biases 0.  Uniforms from a counter-based generator:
+// splitmix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", 2014) of (seed * 0xD1B54A32D192ED03) ^ i for parameter i, top 24
+// bits + 1/2 scaled to (0, 1); the product a (2u - 1) is formed in FP64 and
+// rounded once to FP32, so any IEEE host restatement gives the same bits.
+__device__ __forceinline__ uint64_t mlp_splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_mlp_init(float *theta, uint64_t seed) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= MLP_NPARAMS) return;
+    int fan = 0;  // fan_in + fan_out of the weight matrix holding i, 0 for a bias
+    if (i < OFF_B1) fan = MLP_IN + MLP_H;
+    else if (i >= OFF_W2 && i < OFF_B2) fan = MLP_H + MLP_H;
+    else if (i >= OFF_W3 && i < OFF_B3) fan = MLP_H + MLP_OUT;
+    if (fan == 0) {
+        theta[i] = 0.f;
+        return;
+    }
+    const uint64_t r = mlp_splitmix64((seed * 0xD1B54A32D192ED03ull) ^ (uint64_t)i);
+    const double u = ((double)(r >> 40) + 0.5) * (1.0 / 16777216.0);
+    const double lim = sqrt(6.0 / (double)fan);
+    theta[i] = (float)(lim * (2.0 * u - 1.0));
+}
+
 }  // namespace cheb
 
 using namespace cheb;
 
 extern "C" int cheb_mlp_param_count(void) { return MLP_NPARAMS; }
+
+extern "C" int cheb_mlp_init(float *theta, uint64_t seed, void *stream) {
+    if (!theta) return fail(CHEB_ERR_INVALID, "cheb_mlp_init: theta is NULL");
+    k_mlp_init<<<(MLP_NPARAMS + 255) / 256, 256, 0, as_stream(stream)>>>(theta, seed);
+    return check_launch("k_mlp_init");
+}
 
 extern "C" int cheb_mlp_forward(const float *theta, const float *X, int32_t batch, float *act, float *out,
                                 void *stream) {

@@ -23,6 +23,8 @@
 //      and the moments Tr T_{k+1}, <T_{k+1}, G> are written per panel and step;
 //   D. a second kernel sums the per-panel moments of each system and step in
 //      a fixed order (deterministic).
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "plan.cuh"
@@ -55,7 +57,11 @@ struct ResArgs {
     const int64_t *lrow_base;
     const int32_t *lrow_ptr;
     const uint32_t *lent;
+    int32_t round_bf16;  // CHEB_BF16: every stored T_{k+1} rounded to bfloat16
 };
+
+__device__ __forceinline__ float res_round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ double res_round_bf16(double x) { return x; }
 
 template <typename T>
 __device__ __forceinline__ void r_st(unsigned char *B, int b, const T (&x)[16]);
@@ -323,7 +329,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_resident(const ResArgs<T> a) 
                     for (int i = 0; i < 16; ++i)
                         if (i / EPL == kg) {
                             T *yp = r_el<T>(Yb, b, i);
-                            *yp = T(2) * acc[i] - *yp;
+                            const T v = T(2) * acc[i] - *yp;
+                            *yp = a.round_bf16 ? res_round_bf16(v) : v;
                         }
                 }
             }
@@ -385,9 +392,9 @@ __global__ void k_res_moments(const double *part, int kmax, const int32_t *sys_p
     if (gmom) gmom[(int64_t)sy * mom_stride + k] = g;
 }
 
-__global__ void k_to_f32_res(const double *in, float *out, int64_t n) {
+__global__ void k_to_f32_res(const double *in, float *out, int64_t n, int round_bf16) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (float)in[i];
+    if (i < n) out[i] = round_bf16 ? __bfloat162float(__float2bfloat16_rn(in[i])) : (float)in[i];
 }
 
 template <typename T, int P, int NW, int MINB>
@@ -441,7 +448,7 @@ template <typename T>
 int resident_impl(const cheb_plan *plan, const cheb_bsr *Mt, int kmax, const int32_t *n_terms_dev, int n_single,
                   const double *coeffs, const int64_t *coef_off, int32_t stride, int32_t nf, double *const *acc,
                   double *moments, const double *G, double *gmoments, int mom_stride, void *ws, size_t ws_bytes,
-                  cudaStream_t s) {
+                  cudaStream_t s, int round_bf16 = 0) {
     Carve cv(ws, ws_bytes);
     const T *Lv;
     if (sizeof(T) == 8) {
@@ -449,7 +456,7 @@ int resident_impl(const cheb_plan *plan, const cheb_bsr *Mt, int kmax, const int
     } else {
         float *lv = cv.take<float>(Mt->nnzb * BB);
         const int64_t n = Mt->nnzb * BB;
-        k_to_f32_res<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double *)Mt->vals, lv, n);
+        k_to_f32_res<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double *)Mt->vals, lv, n, round_bf16);
         CHEB_TRY(check_launch("k_to_f32"));
         Lv = reinterpret_cast<const T *>(lv);
     }
@@ -482,6 +489,7 @@ int resident_impl(const cheb_plan *plan, const cheb_bsr *Mt, int kmax, const int
     a.G = G;
     a.part = part;
     a.kmax = kmax;
+    a.round_bf16 = round_bf16;
     CHEB_TRY(run_resident<T>(plan, a, s));
     if (moments || gmoments) {
         const dim3 g((kmax + 127) / 128, plan->nsys);
@@ -528,11 +536,10 @@ extern "C" int cheb_expand(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_
     if (precision == CHEB_F64)
         return resident_impl<double>(plan, Mt, n_terms, nullptr, n_terms, cf, nullptr, coeff_stride, n_f, acc, moments,
                                      G, gmoments, n_terms, ws, ws_bytes, s);
-    if (precision == CHEB_F32)
+    if (precision == CHEB_F32 || precision == CHEB_BF16)
         return resident_impl<float>(plan, Mt, n_terms, nullptr, n_terms, cf, nullptr, coeff_stride, n_f, acc, moments,
-                                    G, gmoments, n_terms, ws, ws_bytes, s);
-    return fail(CHEB_ERR_INVALID, "cheb_expand: unsupported precision %d (CHEB_BF16: cheb_expand_stepwise)",
-                precision);
+                                    G, gmoments, n_terms, ws, ws_bytes, s, precision == CHEB_BF16);
+    return fail(CHEB_ERR_INVALID, "cheb_expand: unsupported precision %d", precision);
 }
 
 extern "C" int cheb_expand_batched(const cheb_plan *plan, const cheb_bsr *Mt, int32_t max_terms,
@@ -554,8 +561,9 @@ extern "C" int cheb_expand_batched(const cheb_plan *plan, const cheb_bsr *Mt, in
     if (precision == CHEB_F64)
         return resident_impl<double>(plan, Mt, max_terms, n_terms, 0, cf, n_f > 0 ? coeff_offset : nullptr,
                                      coeff_stride, n_f, acc, moments, G, gmoments, moment_stride, ws, ws_bytes, s);
-    if (precision == CHEB_F32)
+    if (precision == CHEB_F32 || precision == CHEB_BF16)
         return resident_impl<float>(plan, Mt, max_terms, n_terms, 0, cf, n_f > 0 ? coeff_offset : nullptr,
-                                    coeff_stride, n_f, acc, moments, G, gmoments, moment_stride, ws, ws_bytes, s);
+                                    coeff_stride, n_f, acc, moments, G, gmoments, moment_stride, ws, ws_bytes, s,
+                                    precision == CHEB_BF16);
     return fail(CHEB_ERR_INVALID, "cheb_expand_batched: unsupported precision %d", precision);
 }

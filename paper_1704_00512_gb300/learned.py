@@ -110,15 +110,9 @@ class Proposal:
         self.t = 0
 
     @staticmethod
-    def xavier(seed: int) -> np.ndarray:
-        """Xavier-uniform weights, zero biases (numpy rng; the caller's random numbers)."""
-        rng = np.random.default_rng(seed)
-        parts = []
-        for nout, nin in ((128, 35), (128, 128), (2, 128)):
-            lim = math.sqrt(6.0 / (nin + nout))
-            parts.append(rng.uniform(-lim, lim, size=nout * nin))
-            parts.append(np.zeros(nout))
-        return np.concatenate(parts)
+    def xavier(seed: int, device) -> torch.Tensor:
+        """Xavier-uniform weights, zero biases (cheb_mlp_init on the device)."""
+        return L.mlp_init(seed, device)
 
     def forward(self, X: torch.Tensor) -> torch.Tensor:
         act = torch.empty(X.shape[0] * 256, dtype=torch.float32, device=self.device)

@@ -126,20 +126,27 @@ def powers(pb: Problem, exponents=(-1.0, 0.5, -0.5), tol: float = 1e-10, n_max: 
     return out
 
 
-def orthogonalise(pb: Problem, A: torch.Tensor) -> L.Bsr:
-    """H' = P_H(A P_out(H A)), A = S^-1/2 on P_out."""
+def orthogonalise(pb: Problem, A: torch.Tensor, energy: bool = False):
+    """H' = P_H(A P_out(H A)), A = S^-1/2 on P_out.
+
+    energy=True also returns the energy functional G_H = Z^T of the same
+    product Z = P_out(A P_out(H A)) (<X, G_H> = Tr(P_out(A P_out(X A)) H))."""
     Y = pb.zeros_out()
     Z = pb.zeros_out()
     L.masked_product(pb.plan64, pb.H, A, Y)
     L.masked_product(pb.plan64, pb.P_out.with_vals(A), Y, Z)
-    return pb.P_H.with_vals(L.restrict(pb.P_out.with_vals(Z), pb.P_H))
+    Hp = pb.P_H.with_vals(L.restrict(pb.P_out.with_vals(Z), pb.P_H))
+    return (Hp, L.transpose(pb.plan64, Z)) if energy else Hp
 
 
-def trace_functional(pb: Problem, A: torch.Tensor) -> torch.Tensor:
-    """G with <X, G> = Tr(P_out(A P_out(X A)) S): the transpose of P_out(A P_out(S A))."""
+def trace_functional(pb: Problem, A: torch.Tensor, M: L.Bsr | None = None) -> torch.Tensor:
+    """G with <X, G> = Tr(P_out(A P_out(X A)) M): the transpose of P_out(A P_out(M A)).
+
+    M = S (default) gives the electron count Tr(F S); M = H gives the energy
+    Tr(F H) of the same kernel (M symmetric, its pattern within P_out)."""
     Y = pb.zeros_out()
     Z = pb.zeros_out()
-    L.masked_product(pb.plan64, pb.S, A, Y)
+    L.masked_product(pb.plan64, pb.S if M is None else M, A, Y)
     L.masked_product(pb.plan64, pb.P_out.with_vals(A), Y, Z)
     return L.transpose(pb.plan64, Z)
 
@@ -178,7 +185,7 @@ def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FE
         max_iter: int = 100, form: str = "twopass", n_mu: int = 4, mu_half_kT: float = 0.02,
         overlap: dict | None = None, tol_S: float | None = None, penalty_alpha: float = -200.0,
         penalty_threshold: float = 1.0, penalty_widen: float = 0.05, penalty_terms: int = 512,
-        stepwise: bool = True, isqrt: str = "f64", timings: dict | None = None) -> dict:
+        energy: bool = False, stepwise: bool = True, isqrt: str = "f64", timings: dict | None = None) -> dict:
     """Density matrix F with Tr(F S) = N_e (see the module docstring for the steps).
 
     form: "twopass" (moment pass, bisection, accumulation pass) or "mu4" (a
@@ -190,15 +197,21 @@ def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FE
     the terms it is expanded in, so that the penalty polynomial resolves it):
     a failing bound is widened by penalty_widen of the interval width and pass
     1 repeated once; a second failure raises ChebError(ERR_BOUNDS).
+    energy (two-pass form only): the accumulation pass also collects the
+    energy moments e_k = <T_k, G_H> (G_H the energy functional of the overlap
+    setup), so that Tr(K H) of any kernel re-summed from the same polynomials
+    costs no new products (the beta check of Sec. "Fermi Operator Expansion").
     """
     if form not in ("twopass", "mu4"):
         raise ValueError(f"foe: unknown form {form!r}")
+    if energy and form != "twopass":
+        raise ValueError("foe: the energy moments ride on the second pass of the two-pass form")
     tm = {} if timings is None else timings
     t0 = time.perf_counter()
     tS = tol if tol_S is None else tol_S
     ov = overlap_setup(pb, tS, lanczos_k, bounds_S, n_S, isqrt) if overlap is None else overlap
     A, G = ov["A"], ov["G"]
-    Hp = orthogonalise(pb, A)
+    Hp, GH = orthogonalise(pb, A, True) if energy else (orthogonalise(pb, A), None)
     if bounds_H is None:
         e0, e1, _ = L.bounds(Hp, lanczos_k)
     else:
@@ -236,14 +249,16 @@ def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FE
         if verdict in (1, 2):
             e1 += w
     passes = 1
+    em = None
     if form == "twopass":
         res = L.mu_search(g, n, e0, e1, kind, kT, N_e, tol_N, max_iter)
         r = L.decode_mu_result(res)
         mu = r["mu"]
         _, c = L.coeffs([{"kind": kind, "mu": mu, "kT": kT}], e0, e1, 0.0, n, device=pb.device)
         p = pb.zeros_out()
+        em = torch.zeros(n, dtype=torch.float64, device=pb.device) if energy else None
         ev[2].record()
-        L.expand(pb.planX, Hpt, n, c, [p], precision=pb.precision, ws=ws, stepwise=stepwise)
+        L.expand(pb.planX, Hpt, n, c, [p], G=GH, gmoments=em, precision=pb.precision, ws=ws, stepwise=stepwise)
         ev[3].record()
         passes = 2
         mus, gm = [mu], g
@@ -275,7 +290,60 @@ def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FE
     tm["form"] = form
     return {"F": F, "p": p, "mus": mus, "A": A, "Hp": Hp, "G": G, "mu": mu, "mu_result": r, "mu_half": r_half,
             "moments": t, "gmoments": gm, "n_terms": n, "n_pass1": m, "passes": passes, "bounds_H": (e0, e1),
-            "bounds_S": ov["bounds_S"], "n_S": ov["n_S"], "trace_FS": trFS, "penalty": penalty}
+            "bounds_S": ov["bounds_S"], "n_S": ov["n_S"], "trace_FS": trFS, "penalty": penalty,
+            "emoments": em, "G_H": GH, "kT": kT, "kind": kind, "N_e": N_e, "tol_N": tol_N}
+
+
+def energy_pair(pb: Problem, r: dict, kT_prime: float, max_iter: int = 100) -> dict:
+    """E = Tr(K H) of a two-pass solve r (foe with energy=True) and E' = Tr(K' H)
+    of the kernel K' with the wider smearing kT_prime, both re-summed from r's
+    moments: K' takes its own mu' (bisection on the same trace moments, so that
+    Tr(K' S) = N_e too) and its coefficient set, and no new products."""
+    em = r.get("emoments")
+    if em is None:
+        raise ValueError("energy_pair: the solve did not collect energy moments (foe(..., energy=True))")
+    n, (e0, e1), kind = r["n_terms"], r["bounds_H"], r["kind"]
+    _, c = L.coeffs([{"kind": kind, "mu": r["mu"], "kT": r["kT"]}], e0, e1, 0.0, n, device=pb.device)
+    rp = L.decode_mu_result(L.mu_search(r["gmoments"], n, e0, e1, kind, kT_prime, r["N_e"], r["tol_N"], max_iter))
+    _, cp = L.coeffs([{"kind": kind, "mu": rp["mu"], "kT": kT_prime}], e0, e1, 0.0, n, device=pb.device)
+    E = L.series_value(c[0], em, n)
+    Ep = L.series_value(cp[0], em, n)
+    return {"E": E, "E_prime": Ep, "mu_prime": rp["mu"], "mu_prime_result": rp}
+
+
+def foe_auto_kT(pb: Problem, kT0: float, N_e: float, dE_tol: float, widen: float = 1.25, shrink: float = 0.5,
+                kT_min: float = 1e-4, max_rounds: int = 8, **kw) -> dict:
+    """Smearing chosen on the fly (Sec. "Fermi Operator Expansion"): solve with
+    kT, compare E = Tr(K H) with E' = Tr(K' H) of the same polynomials at
+    kT' = widen kT; accept when |E - E'| <= dE_tol, otherwise solve again with
+    kT <- shrink kT (more terms) until kT_min.  kw goes to foe (two-pass form,
+    energy moments on); the overlap setup and the bounds of H are kept across
+    rounds.  Returns the accepted solve with "kT", "E", "E_prime" and the
+    "rounds" history [(kT, n_terms, E, E', accepted)]."""
+    if not (widen > 1.0 and 0.0 < shrink < 1.0 and dE_tol > 0.0):
+        raise ValueError("foe_auto_kT: need widen > 1, 0 < shrink < 1, dE_tol > 0")
+    kw = dict(kw)
+    if kw.pop("n_H", None) is not None:
+        raise ValueError("foe_auto_kT: the term count follows kT (Eq. 6); n_H cannot be fixed")
+    kw["form"], kw["energy"] = "twopass", True
+    if kw.get("overlap") is None:
+        tS = kw.get("tol_S") or kw.get("tol", 1e-10)
+        kw["overlap"] = overlap_setup(pb, tS, kw.get("lanczos_k", 40), kw.get("bounds_S"), kw.get("n_S"),
+                                      kw.get("isqrt", "f64"))
+    rounds = []
+    kT = kT0
+    while True:
+        r = foe(pb, kT, N_e, **kw)
+        kw["bounds_H"] = r["bounds_H"]
+        ep = energy_pair(pb, r, widen * kT, kw.get("max_iter", 100))
+        E, Ep = float(ep["E"].item()), float(ep["E_prime"].item())
+        ok = abs(E - Ep) <= dE_tol
+        rounds.append((kT, r["n_terms"], E, Ep, ok))
+        if ok or len(rounds) == max_rounds or shrink * kT < kT_min:
+            r.update(ep)
+            r.update({"E": E, "E_prime": Ep, "rounds": rounds, "accepted": ok})
+            return r
+        kT *= shrink
 
 
 def selected_eigenvalues(pb: Problem, kT: float, intervals=(), levels=(), tol: float = 1e-9, n_max: int = 16384,

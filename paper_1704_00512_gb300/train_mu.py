@@ -82,7 +82,7 @@ def main(argv=None):
     perm = np.random.default_rng(args.seed + 1).permutation(n)
     n_hold = max(1, n // 10)
     hold, train = perm[:n_hold], perm[n_hold:]
-    prop = learned.Proposal(learned.Proposal.xavier(args.seed + 2), dev)
+    prop = learned.Proposal(learned.Proposal.xavier(args.seed + 2, dev), dev)
     t0 = time.time()
     hist = prop.train(X[train], xstar[train], scale[train], iters=args.iters, lr=args.lr,
                       log_every=max(1, args.iters // 20))

@@ -24,6 +24,8 @@ def test_workloads_carry_what_their_arm_reads():
             assert {"n_atoms", "r_c", "r_buf", "kT", "N_e", "tol", "tol_S", "n_mu"} <= set(cfg), name
             if cfg.get("form") == "learned":
                 assert cfg["n_mu"] <= 8 and 0 < cfg["max_half_kT"] <= 1.0
+            if cfg.get("form") == "autokT":
+                assert cfg["dE_tol"] > 0 and cfg["widen"] > 1 and 0 < cfg["shrink"] < 1, name
     assert bench.DEFAULT_WORKLOAD in bench.WORKLOADS
 
 

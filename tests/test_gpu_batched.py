@@ -80,6 +80,26 @@ def test_batched_foe_matches_per_system_oracle_and_replays(prec):
     # and so does the eager sequence without graphs
     eager = batched.foe_batched(bp, KT, N_e, tol=1e-9, tol_S=1e-10, tol_N=tolN, use_graphs=False)
     assert torch.equal(eager["F"], out["F"])
+    # a new Hamiltonian in place (every system's H scaled by 1.0003: new bounds,
+    # coefficients and mu, the same term counts): the replayed graphs read the
+    # new values and agree with the eager sequence and with the oracle
+    fac = 1.0003
+    bp.H.vals.mul_(fac)
+    new = batched.foe_batched(bp, KT, N_e, tol=1e-9, tol_S=1e-10, tol_N=tolN)
+    assert not new["captured"] and new["n_terms"] == out["n_terms"]
+    assert new["mu"] != out["mu"]
+    eager2 = batched.foe_batched(bp, KT, N_e, tol=1e-9, tol_S=1e-10, tol_N=tolN, use_graphs=False)
+    assert torch.equal(eager2["F"], new["F"]) and eager2["mu"] == new["mu"]
+    assert [r["bits"] for r in eager2["mu_result"]] == [r["bits"] for r in new["mu_result"]]
+    if prec == cg.F64:
+        F2 = new["F"].cpu().numpy()
+        for i, s in enumerate(systems):
+            S, H, P_out = pipelines.system_mats(s, R_BUF)
+            H = H.with_vals(H.vals * fac)
+            orc = pipelines.foe(S, H, P_out, KT, N_e[i], new["bounds_S"][i], new["n_S"][i], new["bounds_H"][i],
+                                new["n_terms"][i], tol_N=tolN[i])
+            assert relF(F2[bp.ooff[i]:bp.ooff[i + 1]], orc["F"].vals) < 1e-10
+            assert new["mu_result"][i]["bits"] == orc["mu"].bits
 
 
 def test_autotune_caches_a_valid_tile():

@@ -136,3 +136,33 @@ def test_col_kernel_sparse_operator_rows():
     acc, t, g = run(plan, dL, n, coeffs, nf, G, P_out.nnzb, cg.F32)
     assert relF(acc[0].cpu().numpy(), ex.acc[0].vals) < 1e-5
     assert relF(g.cpu().numpy(), ex.g) < 1e-5
+
+
+def test_resident_expansion_bf16_within_bound():
+    # cheb_expand (one launch, panels resident in shared memory) on a CHEB_BF16
+    # plan: Mt and every stored T_k rounded to bfloat16, products summed in FP32
+    n, nf = 48, 2
+    Ht, P_out, coeffs, G = case(200, 5.0, 2.5, 7, n, nf)
+    ex = ref.chebyshev_expand(Ht, P_out, coeffs, G=G)
+    dP = dbsr(P_out.row_ptr, P_out.col_idx)
+    dHt = dbsr(Ht.row_ptr, Ht.col_idx, Ht.vals)
+    plan = cg.Plan(dP, cg.BF16)
+    acc = [torch.zeros((P_out.nnzb, 4, 4), dtype=torch.float64, device=DEV) for _ in range(nf)]
+    t = torch.zeros(n, dtype=torch.float64, device=DEV)
+    cg.expand(plan, dHt, n, torch.as_tensor(coeffs, device=DEV), acc, moments=t, precision=cg.BF16, stepwise=False)
+    u = 2.0 ** -8
+    k = np.arange(n)
+    for j in range(nf):
+        bound = 8 * u * np.sum(np.abs(coeffs[j]) * (1 + k) ** 2) * np.sqrt(P_out.nnzb * 16)
+        err = np.linalg.norm(acc[j].cpu().numpy() - ex.acc[j].vals)
+        assert err < bound, (err, bound)
+    # rounding really happens: farther from the oracle than the FP32 resident run
+    acc32 = [torch.zeros_like(acc[0])]
+    cg.expand(cg.Plan(dP, cg.F32), dHt, n, torch.as_tensor(coeffs[:1], device=DEV), acc32, precision=cg.F32,
+              stepwise=False)
+    e16 = relF(acc[0].cpu().numpy(), ex.acc[0].vals)
+    e32 = relF(acc32[0].cpu().numpy(), ex.acc[0].vals)
+    assert e32 < 1e-5 and e16 > 10 * e32
+    # and the same roundings as the stepwise BF16 form up to FP32 summation order
+    acc_s, _, _ = run(plan, dHt, n, coeffs, nf, G, P_out.nnzb, cg.BF16)
+    assert relF(acc[0].cpu().numpy(), acc_s[0].cpu().numpy()) < 5e-2

@@ -272,6 +272,23 @@ def test_bounds_parity_and_containment():
         assert abs(e0 - o0) < 1e-6 * width and abs(e1 - o1) < 1e-6 * width
 
 
+def test_bounds_warm_start_hull():
+    s, S, H, P_out = setup(300, 6.0, 3.0, 4)
+    dH = dbsr(H.row_ptr, H.col_idx, H.vals)
+    e0, e1, th = cg.bounds(dH, 8)
+    w = np.linalg.eigvalsh(H.dense())
+    assert th[0] >= w[0] - 1e-12 and th[1] <= w[-1] + 1e-12  # Ritz values lie inside the spectrum
+    # a warm interval that contains the Lanczos interval is kept as it is
+    wide = (e0 - 0.3, e1 + 0.2)
+    assert cg.bounds_warm(dH, wide, 8)[:2] == wide
+    # a warm interval that misses it on either side is widened to it there
+    narrow = (0.5 * (e0 + e1) - 0.1, 0.5 * (e0 + e1) + 0.1)
+    assert cg.bounds_warm(dH, narrow, 8)[:2] == (e0, e1)
+    assert cg.bounds_warm(dH, (e0 + 0.05, e1 + 0.5), 8)[:2] == (e0, e1 + 0.5)
+    with pytest.raises(cg.ChebError):
+        cg.bounds_warm(dH, (1.0, 1.0), 8)
+
+
 # --------------------------------------------------------------------------
 # mu search, Newton-Schulz, whole solves
 # --------------------------------------------------------------------------

@@ -6,6 +6,7 @@ same quantity a different way, dense linear algebra, or brute force on tiny
 inputs.  No GPU is needed.
 """
 
+import math
 import os
 
 import numpy as np
@@ -17,7 +18,7 @@ from scipy.spatial import cKDTree
 from scipy.special import iv
 
 import synth
-from oracle import ref
+from oracle import pipelines, ref
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -382,6 +383,73 @@ def test_foe_dense_matches_generalised_eigh():
     Fex = ref.dense_function(Hd, f, Sd)
     assert ref.rel_frobenius(F.dense(), Fex) < 1e-8
     assert abs(ref.trace_product(F, S) - N_e) < 1e-7
+
+
+def _dense_isqrt_case(n_atoms=12, seed=11):
+    s, S, H, P = _dense_foe_case(n_atoms=n_atoms, seed=seed)
+    Sd, Hd = S.dense(), H.dense()
+    ws = np.linalg.eigvalsh(Sd)
+    se0, se1 = 0.95 * ws[0], 1.05 * ws[-1]
+    fpow = ref.Func(ref.KIND_POWER, a=-0.5)
+    n_s = ref.choose_degree(fpow, se0, se1, 1e-13, 4096, rel=True)
+    A = ref.chebyshev_expand(ref.scale(S, se0, se1), P, ref.cheb_coeffs(fpow, n_s, se0, se1)[None]).acc[0]
+    eps = sla.eigh(Hd, Sd, eigvals_only=True)
+    return s, S, H, P, A, eps, ((se0, se1), n_s)
+
+
+def _fermi(x):
+    return 0.5 * (1.0 - np.tanh(0.5 * x))
+
+
+@pytest.mark.parametrize("kind", [ref.KIND_FERMI, ref.KIND_ERFC])
+def test_energy_moments_resum_to_the_eigenvalue_sum(kind):
+    # E = Tr(K H) = sum_i f(eps_i) eps_i over the generalised eigenvalues (K
+    # built from c_i with c^T S c = 1): the energy moments re-summed with the
+    # coefficients of any (mu, kT) -- a second kernel costs no new products.
+    s, S, H, P, A, eps, _ = _dense_isqrt_case()
+    Hp = ref.orthogonalise(H, A, P)
+    e0, e1 = eps[0] - 0.1, eps[-1] + 0.1
+    GH = ref.trace_functional_matrix(A, H, P)
+    n = ref.choose_degree(ref.Func(kind, mu=0.5 * (e0 + e1), kT=0.02), e0, e1, 1e-12, 16384)
+    e = ref.chebyshev_expand(ref.scale(Hp, e0, e1), P, np.zeros((1, n)), G=GH).g
+    occ = _fermi if kind == ref.KIND_FERMI else (lambda x: 0.5 * erfc_vec(x))
+    for mu, kT in ((float(np.median(eps)), 0.02), (float(eps[10]), 0.05), (float(eps[30]), 0.03)):
+        E = ref.energy(e, ref.Func(kind, mu=mu, kT=kT), e0, e1)
+        want = float(np.sum(occ((eps - mu) / kT) * eps))
+        assert abs(E - want) < 1e-8 * max(1.0, abs(want)), (mu, kT, E, want)
+    # the electron-count functional on the same moments is a different number
+    G = ref.trace_functional_matrix(A, S, P)
+    g = ref.chebyshev_expand(ref.scale(Hp, e0, e1), P, np.zeros((1, n)), G=G).g
+    assert abs(ref.energy(g, ref.Func(kind, mu=float(np.median(eps)), kT=0.02), e0, e1) - want) > 1e-3
+
+
+def erfc_vec(x):
+    return np.array([math.erfc(v) for v in np.ravel(x)]).reshape(np.shape(x))
+
+
+def test_auto_kT_matches_brute_force_on_eigenvalues():
+    # The oracle's smearing loop against the same loop run on the generalised
+    # eigenvalues: mu(kT) from sum f = N_e, E = sum f eps, the same rule.
+    s, S, H, P, A, eps, (bS, n_S) = _dense_isqrt_case()
+    N_e = float(len(eps) // 2)
+    e0, e1 = eps[0] - 0.1, eps[-1] + 0.1
+    kT0, widen, shrink = 0.2, 1.25, 0.5
+
+    def exact(kT):
+        mu = brentq(lambda m: np.sum(_fermi((eps - m) / kT)) - N_e, e0, e1, xtol=1e-14)
+        return float(np.sum(_fermi((eps - mu) / kT) * eps))
+
+    dE = [abs(exact(kT0 * shrink ** r) - exact(widen * kT0 * shrink ** r)) for r in range(4)]
+    assert dE[0] > dE[1] > dE[2]  # the difference shrinks with the smearing
+    dE_tol = float(np.sqrt(dE[1] * dE[2]))  # accept in the third round, far from the edge
+    out = pipelines.foe_auto_kT(S, H, P, kT0, N_e, dE_tol, bS, n_S, (e0, e1), 1e-11, 16384, 1e-10 * N_e,
+                                widen=widen, shrink=shrink)
+    assert [r[0] for r in out["rounds"]] == [kT0, kT0 * shrink, kT0 * shrink ** 2]
+    assert [r[4] for r in out["rounds"]] == [False, False, True] and out["accepted"]
+    for r, k in zip(out["rounds"], range(3)):
+        kT = kT0 * shrink ** k
+        assert abs(r[2] - exact(kT)) < 1e-7 * N_e and abs(r[3] - exact(widen * kT)) < 1e-7 * N_e
+    assert abs(out["trace_FS"] - N_e) < 1e-7 * N_e
 
 
 def test_trace_functional_is_adjoint_of_postprocessing():

@@ -77,3 +77,28 @@ def test_adam_first_step_is_signed_lr():
 def test_features():
     f = mlp.features(np.arange(40.0), 10, -8.0, 9.0, 5.0)
     assert f.shape == (35,) and f[31] == 3.1 and f[32] == -0.8 and f[33] == 0.9 and f[34] == 0.5
+
+
+def test_splitmix64_published_sequence():
+    # the first three outputs of SplitMix64 from state 0 (state advances by the
+    # golden-ratio increment each call)
+    g = np.uint64(0x9E3779B97F4A7C15)
+    with np.errstate(over="ignore"):
+        states = np.array([0, g, g + g], dtype=np.uint64)
+    out = [int(v) for v in mlp.splitmix64(states)]
+    assert out == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_xavier_init_range_and_variance():
+    th = mlp.xavier_init(3).astype(np.float64)
+    p = mlp.unpack(th)
+    for w, b in (("W1", "b1"), ("W2", "b2"), ("W3", "b3")):
+        W = p[w]
+        a = np.sqrt(6.0 / (W.shape[0] + W.shape[1]))
+        assert np.all(p[b] == 0.0) and np.all(np.abs(W) < a)
+        # U(-a, a): mean 0, variance a^2/3 = 2/(fan_in + fan_out)
+        n = W.size
+        assert abs(W.mean()) < 4 * a / np.sqrt(3 * n)
+        assert abs(W.var() / (a * a / 3) - 1) < 4 * np.sqrt(0.8 / n)
+    assert not np.array_equal(th, mlp.xavier_init(4))
+    assert np.array_equal(th, mlp.xavier_init(3).astype(np.float64))
