@@ -40,6 +40,18 @@ import numpy as np  # noqa: E402
 METRIC = "density-matrix solves/s at <=1e-6 vs FP64 plain; masked SpGEMM HBM GB/s"
 UNIT = "solves/s"
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# column-order step kernel, from one ncu capture of every k_colstep launch of a
+# 4-mu solve on 3,000 atoms (12,000 rows, r_c 10, r_out 14 bohr: 1,183,812
+# P_out blocks; pass 1 moments only, pass 2 four accumulators; grouped steps
+# included), GB300.  Per-launch traffic scales with the P_out blocks (the
+# operator has the same share of them).  Valid only for the kernel source it was
+# measured on: the sha256 of colstep.cu's text before its host-builder section
+# (the kernels and their launch code); after any change there the bench reports
+# traffic null.
+COL_KERNEL_END = "// Host: the column kernel's panels and work streams"
+COL_TRAFFIC = {"colstep_sha256": "cc9d95ecc1b85669fcea8afd64036312d5f218382ae48e929d2b0e3a7ef74bb3",
+               "blocks_P_out": 1183812, "pass1_bytes": 463.3e6, "pass2_4acc_bytes": 866.2e6}
 SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 
 WORKLOADS = {
@@ -74,6 +86,10 @@ WORKLOADS = {
     # Matrix powers S^-1, S^1/2, S^-1/2 from one shared FP64 recursion: 3,000
     # atoms x 4 (12,000 rows), 10 bohr cutoff, 4 bohr output buffer.
     "powers_fp64_12k": dict(powers=True, n_atoms=3000, r_c=10.0, r_buf=4.0, tol=1e-10, precision="f64", n_mu=3,
+                            exponents=(-1.0, 0.5, -0.5)),
+    # The same powers with FP64-accurate double-float products on the FP32 pipe
+    # (CHEB_F64X), timed against the FP64 (DFMA) expansion in the same run.
+    "powers_f64x_12k": dict(powers=True, n_atoms=3000, r_c=10.0, r_buf=4.0, tol=1e-10, precision="f64x", n_mu=3,
                             exponents=(-1.0, 0.5, -0.5)),
     # Batched: 64 independent systems of U{125..1500} atoms (seeds 0..63), 8 bohr
     # cutoff, each with its own bounds, degree and mu; both passes one launch
@@ -384,8 +400,9 @@ def run_cheb(args, rank: int, world: int, local: int):
         gbs = alg_bytes / (avg_ms / 1e3) / 1e9
         alu_peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
         hbm_peak, hbm_src = measured_hbm_peak()
+        traffic = col_traffic_per_launch(form, cfg["n_mu"], launches_pass, nnz_out)
         roof = {"bound": "alu", "achieved": round(tflops, 3), "peak": round(alu_peak, 3), "unit": "TFLOP/s",
-                "frac": round(tflops / alu_peak, 4), "traffic": None,
+                "frac": round(tflops / alu_peak, 4), "traffic": traffic,
                 "peak_source": "FP32 FMA unit count: 152 SMs x 128 lanes x 2 flops x 2070 MHz",
                 "kernel": "k_colstep<4,16,*>", "algorithmic_flops_per_launch": flops,
                 "algorithmic_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(avg_ms, 5),
@@ -462,12 +479,13 @@ def run_powers(args, rank: int, world: int, local: int):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     cfg = WORKLOADS[args.workload]
+    prec = cg.F64X if cfg["precision"] == "f64x" else cg.F64
     sysm = synth.make_system(cfg["n_atoms"], cfg["r_c"], seed=system_seed(rank))
-    pb = solve.problem_from_system(sysm, cfg["r_buf"], dev, cg.F64)
+    pb = solve.problem_from_system(sysm, cfg["r_buf"], dev, prec)
 
-    def step():
+    def step(precision=prec):
         pb.build_patterns()
-        return solve.powers(pb, exponents=cfg["exponents"], tol=cfg["tol"], n_max=512)
+        return solve.powers(pb, exponents=cfg["exponents"], tol=cfg["tol"], n_max=512, precision=precision)
 
     for i in range(args.warmup):
         out = step()
@@ -508,18 +526,42 @@ def run_powers(args, rank: int, world: int, local: int):
     # FLOPs of the n-2 recursion steps over the whole step time (bounds and
     # coefficients included, so a lower bound on the kernel's rate)
     tflops = 2.0 * 64.0 * triples * (n_terms - 2) / (t_ms / args.steps / 1e3) / 1e12
+    if prec == cg.F64X:
+        # the same step with FP64 (DFMA) products, timed here, and the distance
+        # between the two results
+        torch.cuda.synchronize()
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d0.record()
+        o64 = step(cg.F64)
+        d1.record()
+        torch.cuda.synchronize()
+        ms64 = d0.elapsed_time(d1)
+        rel = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(out["acc"], o64["acc"]))
+        alu_peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(alu_peak, 3), "unit": "TFLOP/s",
+                "frac": round(tflops / alu_peak, 4), "traffic": None, "kernel": "k_step<dfl,2,8>",
+                "peak_source": "FP32 FMA unit count: 152 SMs x 128 lanes x 2 flops x 2070 MHz (the pipe the "
+                               "double-float products run on; achieved counts FP64-accurate flops)",
+                "vs_fp64_unit_peak": round(tflops / FP64_NOMINAL_TFLOPS, 3)}
+        vs_dfma = {"fp64_dfma_step_ms": round(ms64, 2), "f64x_step_ms": round(t_ms / args.steps, 2),
+                   "speedup": round(ms64 / (t_ms / args.steps), 3), "max_relF_vs_fp64": rel}
+    else:
+        roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(tflops / FP64_NOMINAL_TFLOPS, 4), "traffic": None,
+                "kernel": "k_step<double,2,8>",
+                "peak_source": "FP64 unit count: 304 DFMA lanes per cycle x 2 flops x 2070 MHz"}
+        vs_dfma = None
     res = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 2), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == cg.F64 else "f32x2 (double-float)",
+        "data": "synthetic",
         "config": {"workload": args.workload, "atoms_per_gpu": cfg["n_atoms"], "rows": 4 * cfg["n_atoms"],
                    "r_c": cfg["r_c"], "r_buf": cfg["r_buf"], "exponents": list(cfg["exponents"]), "n_terms": n_terms,
                    "fit_tol": cfg["tol"], "blocks_P_H": pb.P_H.nnzb, "blocks_P_out": pb.P_out.nnzb,
                    "triples": triples, "l2": "inputs larger than L2 (no flush)"},
-        "roofline": {"bound": "alu", "achieved": round(tflops, 4), "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": round(tflops / FP64_NOMINAL_TFLOPS, 4), "traffic": None,
-                     "kernel": "k_step<double,2,8>",
-                     "peak_source": "FP64 unit count: 304 DFMA lanes per cycle x 2 flops x 2070 MHz"},
+        "roofline": roof,
+        "vs_fp64_dfma": vs_dfma,
         "e2e": {"value": round(job_throughput(args.e2e_steps, world, te_ms), 4), "unit": UNIT,
                 "h2d_bytes_per_step": int(h_S.numel() * 8), "d2h_bytes_per_step": int(sum(h.numel() for h in h_out) * 8)},
         "gpu_launches": int(launches), "clocks": clocks,
@@ -653,6 +695,26 @@ def oracle_threads() -> int:
         return max(1, int(os.environ["OMP_NUM_THREADS"]))
     except (KeyError, ValueError):
         return os.cpu_count() or 1
+
+
+def col_traffic_per_launch(form: str, n_mu: int, launches_pass, nnz_out: int):
+    """Measured DRAM bytes per k_colstep launch of a 4-mu solve, scaled to this
+    system's P_out blocks and averaged over the solve's two passes; None for
+    other forms or when the kernel source differs from the measured one."""
+    import hashlib
+    if form != "mu4" or n_mu != 4 or len(launches_pass) != 2:
+        return None
+    src = os.path.join(ROOT, "paper_1704_00512_gb300", "csrc", "colstep.cu")
+    with open(src, encoding="utf-8") as f:
+        text = f.read()
+    if COL_KERNEL_END not in text:
+        return None
+    kernel = text[:text.index(COL_KERNEL_END)]
+    if hashlib.sha256(kernel.encode()).hexdigest() != COL_TRAFFIC["colstep_sha256"]:
+        return None
+    scale = nnz_out / COL_TRAFFIC["blocks_P_out"]
+    per = [COL_TRAFFIC["pass1_bytes"], COL_TRAFFIC["pass2_4acc_bytes"]]
+    return int(scale * sum(b * n for b, n in zip(per, launches_pass)) / sum(launches_pass))
 
 
 def solve_step_equivalents(n_terms: int, n_pass1: int, nnz_out: int, nnz_H: int) -> float:

@@ -50,7 +50,7 @@ enum {
 };
 
 /* Element types of matrix values. */
-enum { CHEB_F64 = 0, CHEB_F32 = 1, CHEB_BF16 = 2 };
+enum { CHEB_F64 = 0, CHEB_F32 = 1, CHEB_BF16 = 2, CHEB_F64X = 3 };
 
 /* Function kinds for cheb_func.kind (all in the unscaled variable x). */
 enum {
@@ -178,8 +178,26 @@ int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, size_t *op_ws_
  * built (and the ranking kernel runs) when one column's rows do not fit it
  * or the operator has 2^22 - 1 blocks or more.  cheb_plan_col_info reports
  * its panel count (0 when not built), largest union and total operator
- * entries (padding included). */
+ * entries (padding included).
+ *
+ * This gather plan is built by device kernels from the device patterns of
+ * P_out and the operator (a sequential panel walk in one thread block, then
+ * one thread block per panel: union bitmap and ranks, per-row entry counts, the
+ * rows dealt to the warps by decreasing chunk count, each to the warp with the
+ * fewest chunks so far, and the entry streams; a few scalars and per-panel
+ * maxima come back to the host to size the lists).  It uses device memory of
+ * its own until cheb_plan_bind_operator copies the lists into the operator
+ * workspace.  cheb_plan_set_gather_builder(plan, 1), before attaching, builds
+ * the same lists on host threads instead (the reference builder; the two are
+ * bit-identical).  cheb_plan_col_lists_copy copies bound list `which` (0
+ * panels int32[4 per panel], 1 warp chunk starts and 2 warp row starts
+ * int32[panels][17], 3 row words, 4 entry words uint32, 5 slots uint16[nnzb])
+ * into device memory dst (dst_bytes); *bytes receives its size (dst NULL: size
+ * only).  Asynchronous. */
 int cheb_plan_col_info(const cheb_plan *plan, int64_t *n_panels, int32_t *max_union, int64_t *n_entries);
+int cheb_plan_set_gather_builder(cheb_plan *plan, int32_t host);
+int cheb_plan_col_lists_copy(const cheb_plan *plan, int32_t which, void *dst, size_t dst_bytes, size_t *bytes,
+                             void *stream);
 int cheb_plan_bind_operator(cheb_plan *plan, void *op_ws, size_t op_ws_bytes, void *stream);
 int cheb_plan_destroy(cheb_plan *plan);
 

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcheb.so")
 
 OK, ERR_INVALID, ERR_CUDA, ERR_NOT_SPD, ERR_BOUNDS, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_NOSPACE = range(8)
-F64, F32, BF16 = 0, 1, 2
+F64, F32, BF16, F64X = 0, 1, 2, 3  # F64X: FP64-accurate double-float products on the FP32 pipe
 FERMI, ERFC, POWER, INTERVAL, PENALTY = 0, 1, 2, 3, 4
 
 # Every symbol declared in include/cheb.h.
@@ -34,7 +34,7 @@ EXPORTS = [
     "cheb_masked_product", "cheb_transpose", "cheb_restrict", "cheb_trace_workspace_size", "cheb_trace",
     "cheb_penalty_trace", "cheb_mu_search", "cheb_mu_search_noalloc", "cheb_newton_schulz", "cheb_newton_schulz_isqrt",
     "cheb_plan_col_info", "cheb_penalty_check", "cheb_mu_nodes", "cheb_lagrange_weights", "cheb_bounds_spd",
-    "cheb_series_value", "cheb_bounds_warm",
+    "cheb_series_value", "cheb_bounds_warm", "cheb_plan_set_gather_builder", "cheb_plan_col_lists_copy",
 ]
 
 
@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
         "cheb_penalty_check": ([p, i32, dbl, dbl, P(dbl), P(i32), p, sz, p], i32),
         "cheb_mu_nodes": ([dbl, dbl, i32, P(dbl)], i32),
         "cheb_series_value": ([p, p, i32, p, p], i32),
+        "cheb_plan_set_gather_builder": ([p, i32], i32),
+        "cheb_plan_col_lists_copy": ([p, i32, p, ctypes.c_size_t, P(ctypes.c_size_t), p], i32),
         "cheb_bounds_warm": ([P(CBsr), i32, p, dbl, P(dbl), P(dbl), P(dbl), P(dbl), p, ctypes.c_size_t, p], i32),
         "cheb_lagrange_weights": ([P(dbl), i32, dbl, P(dbl)], i32),
         "cheb_bounds_spd": ([P(CBsr), i32, p, dbl, P(dbl), P(dbl), p, sz, p], i32),
@@ -231,11 +233,17 @@ class Plan:
         self._ws = _ws(nbytes.value, P_out.row_ptr.device)
         _check(lib.cheb_plan_bind(h, ctypes.c_void_p(_aligned(self._ws)), nbytes.value, s))
 
-    def attach_operator(self, L: Bsr, stream=None) -> "Plan":
-        """cheb_plan_attach_operator + cheb_plan_bind_operator: row lists for operator pattern L."""
+    def attach_operator(self, L: Bsr, stream=None, gather: str = "device") -> "Plan":
+        """cheb_plan_attach_operator + cheb_plan_bind_operator: row lists for operator pattern L.
+
+        gather: "device" (the gather-plan kernels) or "host" (the reference host
+        builder) for the column-order kernel's lists."""
         lib = load()
         nbytes = ctypes.c_size_t(0)
         s = _stream(stream)
+        if gather not in ("device", "host"):
+            raise ValueError(f"attach_operator: gather must be 'device' or 'host', not {gather!r}")
+        _check(lib.cheb_plan_set_gather_builder(self.handle, 1 if gather == "host" else 0))
         cb = L.c()
         _check(lib.cheb_plan_attach_operator(self.handle, ctypes.byref(cb), ctypes.byref(nbytes), s))
         self._op_ws = _ws(nbytes.value, L.row_ptr.device)
@@ -377,6 +385,19 @@ def plan_col_info(plan: Plan) -> tuple[int, int, int]:
     a, b, c = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
     _check(load().cheb_plan_col_info(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def plan_col_lists(plan: Plan, stream=None) -> list[torch.Tensor]:
+    """cheb_plan_col_lists_copy of all six column-kernel lists, as device byte tensors."""
+    lib = load()
+    out = []
+    for which in range(6):
+        nb = ctypes.c_size_t(0)
+        _check(lib.cheb_plan_col_lists_copy(plan.handle, which, None, 0, ctypes.byref(nb), _stream(stream)))
+        t = torch.empty(max(nb.value, 1), dtype=torch.uint8, device=plan.P_out.row_ptr.device)
+        _check(lib.cheb_plan_col_lists_copy(plan.handle, which, _ptr(t), t.numel(), ctypes.byref(nb), _stream(stream)))
+        out.append(t[:nb.value])
+    return out
 
 
 def plan_resident_info(plan: Plan) -> tuple[int, int, int]:

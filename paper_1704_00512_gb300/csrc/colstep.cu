@@ -847,6 +847,17 @@ static void col_fill(const ColLists &c, const std::vector<int64_t> &rp, const st
     }
 }
 
+// Union rows a panel of the column kernel may hold: shared memory, and slots
+// below 2^COL_SLOT_BITS.
+int32_t col_ucap() {
+    int lo = 0, hi = 65535;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (col_layout(mid, COL_P, COL_NW).total <= (size_t)CHEB_MAX_DYN_SMEM - 1024) lo = mid; else hi = mid - 1;
+    }
+    return std::min(lo, (1 << COL_SLOT_BITS) - 1);
+}
+
 int col_build(cheb_plan *plan, const std::vector<int64_t> &rp, const std::vector<int32_t> &ci,
               const std::vector<int64_t> &lrp, const std::vector<int32_t> &lci) {
     ColLists c;
@@ -854,14 +865,7 @@ int col_build(cheb_plan *plan, const std::vector<int64_t> &rp, const std::vector
     c.NW = COL_NW;
     const int CW = COL_EK * 32 / c.P;  // entries per chunk
     const int64_t nbr = plan->nbr, nnzb = plan->nnzb;
-    {
-        int lo = 0, hi = 65535;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) / 2;
-            if (col_layout(mid, c.P, c.NW).total <= (size_t)CHEB_MAX_DYN_SMEM - 1024) lo = mid; else hi = mid - 1;
-        }
-        c.ucap = std::min(lo, (1 << COL_SLOT_BITS) - 1);
-    }
+    c.ucap = col_ucap();
     // entries pack the operator block index (the appended zero block included)
     // above the union slot
     if ((int64_t)lci.size() + 1 >= ((int64_t)1 << (32 - COL_SLOT_BITS))) return CHEB_ERR_NOSPACE;
@@ -926,6 +930,8 @@ int col_build(cheb_plan *plan, const std::vector<int64_t> &rp, const std::vector
     c.h_rows.swap(rows);
     c.h_ent.swap(ent);
     c.h_slot.swap(slot);
+    c.n_rows = (int64_t)c.h_rows.size();
+    c.n_slot = (int64_t)c.h_slot.size();
     c.built = true;
     plan->col = std::move(c);
     return CHEB_OK;
@@ -933,6 +939,21 @@ int col_build(cheb_plan *plan, const std::vector<int64_t> &rp, const std::vector
 
 int col_bind(ColLists &c, Carve &cv, cudaStream_t s) {
     if (!c.built) return CHEB_OK;
+    if (c.device) {
+        // lists built on the device: one copy of their block into the workspace
+        // (the same carve order, so every array keeps its offset)
+        char *dst = cv.take<char>(c.bytes());
+        if (!cv.fits()) return fail(CHEB_ERR_NOSPACE, "cheb_plan_bind_operator: workspace too small");
+        CHEB_CUDA(cudaMemcpyAsync(dst, c.tmp, c.bytes(), cudaMemcpyDeviceToDevice, s));
+        const ptrdiff_t d = dst - static_cast<char *>(c.tmp);
+        c.d_panels = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(c.d_panels) + d);
+        c.d_wchunk = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(c.d_wchunk) + d);
+        c.d_wrow = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(c.d_wrow) + d);
+        c.d_rows = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(c.d_rows) + d);
+        c.d_ent = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(c.d_ent) + d);
+        c.d_slot = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(c.d_slot) + d);
+        return CHEB_OK;
+    }
     c.d_panels = cv.take<int32_t>(c.h_panels.size());
     c.d_wchunk = cv.take<int32_t>(c.h_wchunk.size());
     c.d_wrow = cv.take<int32_t>(c.h_wrow.size());
@@ -951,7 +972,13 @@ int col_bind(ColLists &c, Carve &cv, cudaStream_t s) {
     return CHEB_OK;
 }
 
+void col_free(ColLists &c) {
+    if (c.tmp) cudaFree(c.tmp);
+    c.tmp = nullptr;
+}
+
 void col_release_host(ColLists &c) {
+    col_free(c);  // (after the stream has been synchronised)
     std::vector<int32_t>().swap(c.h_wchunk);
     std::vector<int32_t>().swap(c.h_wrow);
     std::vector<uint32_t>().swap(c.h_rows);

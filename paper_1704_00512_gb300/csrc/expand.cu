@@ -66,6 +66,7 @@ struct StepArgs {
 // x rounded to the nearest bfloat16 (ties to even), returned as float
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ double bf16_round(double x) { return x; }
+__device__ __forceinline__ dfl bf16_round(dfl x) { return x; }
 
 template <typename T, int P, int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) acc[4 * r + c] = fma(h[4 * r + m], x[c], acc[4 * r + c]);
+                        for (int c = 0; c < 4; ++c) acc[4 * r + c] = mac(h[4 * r + m], x[c], acc[4 * r + c]);
                 }
             }
         };
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
 #pragma unroll
             for (int t = 0; t < EX; ++t)
 #pragma unroll
-                for (int i = 0; i < 16; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], P << t);
+                for (int i = 0; i < 16; ++i) acc[i] += shfl_xor_t(acc[i], P << t);
 #pragma unroll
             for (int l = 0; l < LV; ++l) {
                 const int bit = LKG - 1 - l, n = 16 >> (l + 1);
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_step(const StepArgs<T> a) {
 #pragma unroll
                 for (int j = 0; j < n; ++j) {
                     const T mine = hi ? acc[n + j] : acc[j], other = hi ? acc[j] : acc[n + j];
-                    acc[j] = mine + __shfl_xor_sync(0xffffffffu, other, P << bit);
+                    acc[j] = mine + shfl_xor_t(other, P << bit);
                 }
             }
             const int o = q < ncols && (kg & ((1 << EX) - 1)) == 0 ? oslot[s * P + q] : -1;
@@ -591,6 +592,13 @@ __global__ void __launch_bounds__(NT) k_init(const int64_t *rp, const int32_t *c
     finish_moments<NT, 4>(a.part, a.counter, mm, red);
 }
 
+// FP64 values split into double-floats (hi = the nearest float, lo = the
+// nearest float to the remainder)
+__global__ void k_to_dfl(const double *in, dfl *out, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = dfl(in[i]);
+}
+
 __global__ void k_to_f32(const double *in, float *out, int64_t n, int round_bf16) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = round_bf16 ? __bfloat162float(__float2bfloat16_rn(in[i])) : (float)in[i];
@@ -642,6 +650,18 @@ int run_step<double>(const cheb_plan *plan, const StepArgs<double> &a, cudaStrea
     }
 }
 template <>
+int run_step<dfl>(const cheb_plan *plan, const StepArgs<dfl> &a, cudaStream_t s) {
+    // FP64-accurate plans share the FP64 tile shapes (8-byte elements)
+    switch (plan->tile) {
+        CHEB_TILE_CASE(dfl, TILES_F64, 0)
+        CHEB_TILE_CASE(dfl, TILES_F64, 1)
+        CHEB_TILE_CASE(dfl, TILES_F64, 2)
+        CHEB_TILE_CASE(dfl, TILES_F64, 3)
+        CHEB_TILE_CASE(dfl, TILES_F64, 4)
+        default: return fail(CHEB_ERR_INVALID, "bad FP64 tile %d", plan->tile);
+    }
+}
+template <>
 int run_step<float>(const cheb_plan *plan, const StepArgs<float> &a, cudaStream_t s) {
     static_assert(N_TILES_F32 == 6, "tile table size");
     switch (plan->tile) {
@@ -657,12 +677,13 @@ int run_step<float>(const cheb_plan *plan, const StepArgs<float> &a, cudaStream_
 #undef CHEB_TILE_CASE
 
 size_t expand_ws(const cheb_plan *plan, int64_t nnzL, int precision) {
-    const size_t esz = precision == CHEB_F64 ? 8 : 4;
+    const size_t esz = (precision == CHEB_F64 || precision == CHEB_F64X) ? 8 : 4;
     size_t b = 3 * align_up(plan->nnzb * BB * esz);
     if (precision != CHEB_F64) b += align_up(nnzL * BB * esz);
     b += align_up(plan->n_panels * 4 * sizeof(double)) + align_up(64);
     b += 256;
-    if (precision != CHEB_F64 && plan->col.built) b = std::max(b, col_expand_ws(plan, nnzL));
+    if ((precision == CHEB_F32 || precision == CHEB_BF16) && plan->col.built)
+        b = std::max(b, col_expand_ws(plan, nnzL));
     return b;
 }
 
@@ -674,12 +695,19 @@ int expand_impl(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_terms, cons
     T *buf[3];
     for (int i = 0; i < 3; ++i) buf[i] = cv.take<T>(plan->nnzb * BB);
     const T *Lv;
-    if (sizeof(T) == 8) {
+    const int64_t nL = Mt->nnzb * BB;
+    if constexpr (std::is_same_v<T, double>) {
         Lv = reinterpret_cast<const T *>(Mt->vals);
+    } else if constexpr (std::is_same_v<T, dfl>) {
+        dfl *lv = cv.take<dfl>(nL);
+        if (!cv.fits()) return fail(CHEB_ERR_NOSPACE, "cheb_expand_stepwise: workspace too small");
+        k_to_dfl<<<(unsigned)((nL + 255) / 256), 256, 0, s>>>((const double *)Mt->vals, lv, nL);
+        CHEB_TRY(check_launch("k_to_dfl"));
+        Lv = lv;
     } else {
-        float *lv = cv.take<float>(Mt->nnzb * BB);
-        int64_t n = Mt->nnzb * BB;
-        k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double *)Mt->vals, lv, n, round_bf16);
+        float *lv = cv.take<float>(nL);
+        if (!cv.fits()) return fail(CHEB_ERR_NOSPACE, "cheb_expand_stepwise: workspace too small");
+        k_to_f32<<<(unsigned)((nL + 255) / 256), 256, 0, s>>>((const double *)Mt->vals, lv, nL, round_bf16);
         CHEB_TRY(check_launch("k_to_f32"));
         Lv = reinterpret_cast<const T *>(lv);
     }
@@ -749,6 +777,9 @@ extern "C" int cheb_expand_stepwise(const cheb_plan *plan, const cheb_bsr *Mt, i
     if (precision == CHEB_F64)
         return expand_impl<double>(plan, Mt, n_terms, coeffs, coeff_stride, n_f, acc, moments, G, gmoments, ws,
                                    ws_bytes, s);
+    if (precision == CHEB_F64X)
+        return expand_impl<dfl>(plan, Mt, n_terms, coeffs, coeff_stride, n_f, acc, moments, G, gmoments, ws,
+                                ws_bytes, s);
     if ((precision == CHEB_F32 || precision == CHEB_BF16) && col_usable(plan, Mt))
         return col_expand(plan, Mt, n_terms, coeffs, coeff_stride, n_f, acc, moments, G, gmoments, ws, ws_bytes, s,
                           precision == CHEB_BF16);

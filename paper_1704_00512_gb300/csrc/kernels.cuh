@@ -1,11 +1,81 @@
 // Device helpers shared by the recursion kernels (expand.cu, resident.cu).
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace cheb {
 
 constexpr int MAX_F = 8;  // accumulators (functions / mu values) per expansion
+
+// ---------------------------------------------------------------------------
+// Double-float: a value carried as the unevaluated sum hi + lo of two floats
+// (|lo| <= ulp(hi)/2 when normalised), about 48 significant bits, with every
+// operation on the FP32 pipe.  Building blocks: Knuth's TwoSum (the exact
+// rounding error of a + b in six additions, no ordering needed), the fast
+// two-sum for |a| >= |b| (Dekker 1971, three additions) and the exact product
+// error fma(a, b, -a*b).  GB300 runs FP64 FMA at 1/64 of the FP32 rate, so
+// FP64-accurate block products are cheaper this way.
+struct __align__(8) dfl {
+    float hi, lo;
+    dfl() = default;
+    __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+    __device__ __forceinline__ dfl(int v) : hi((float)v), lo(0.f) {}
+    __device__ __forceinline__ dfl(double v) {
+        hi = __double2float_rn(v);
+        lo = __double2float_rn(v - (double)hi);
+    }
+    __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return dfl(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ dfl df_fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return dfl(s, b - (s - a));
+}
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
+    const dfl s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));  // lo * lo (2^-48 relative) dropped
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfl &operator+=(dfl &a, dfl b) { return a = a + b; }
+
+// acc + h x for the long sums of the block products: the product's exact
+// error and cross terms and the sum's TwoSum error collect in lo, which is
+// left unnormalised (the next TwoSum on hi is exact for any magnitudes); the
+// row-end additions normalise.
+__device__ __forceinline__ dfl mac(dfl h, dfl x, dfl acc) {
+    const float p = h.hi * x.hi;
+    float e = fmaf(h.hi, x.hi, -p);
+    e = fmaf(h.hi, x.lo, fmaf(h.lo, x.hi, e));
+    const dfl s = df_two_sum(acc.hi, p);
+    return dfl(s.hi, s.lo + (acc.lo + e));
+}
+__device__ __forceinline__ float mac(float h, float x, float acc) { return fmaf(h, x, acc); }
+__device__ __forceinline__ double mac(double h, double x, double acc) { return fma(h, x, acc); }
+
+__device__ __forceinline__ float shfl_xor_t(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ double shfl_xor_t(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ dfl shfl_xor_t(dfl v, int m) {
+    return dfl(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+}
+
+// two consecutive double-floats <-> one 16-byte vector
+__device__ __forceinline__ void df_unpack(dfl &a, dfl &b, float4 v) {
+    a = dfl(v.x, v.y);
+    b = dfl(v.z, v.w);
+}
+__device__ __forceinline__ float4 df_pack(dfl a, dfl b) { return make_float4(a.hi, a.lo, b.hi, b.lo); }
 
 template <typename T>
 __device__ __forceinline__ void load16(T (&h)[16], const T *p);
@@ -28,6 +98,13 @@ __device__ __forceinline__ void load16<double>(double (&h)[16], const double *p)
     }
 }
 
+template <>
+__device__ __forceinline__ void load16<dfl>(dfl (&h)[16], const dfl *p) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) df_unpack(h[2 * i], h[2 * i + 1], __ldg(q + i));
+}
+
 template <typename T>
 __device__ __forceinline__ void lds4(T (&x)[4], const T *p);
 template <>
@@ -40,6 +117,13 @@ __device__ __forceinline__ void lds4<double>(double (&x)[4], const double *p) {
     double2 a = *reinterpret_cast<const double2 *>(p);
     double2 b = *reinterpret_cast<const double2 *>(p + 2);
     x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+}
+
+template <>
+__device__ __forceinline__ void lds4<dfl>(dfl (&x)[4], const dfl *p) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    df_unpack(x[0], x[1], q[0]);
+    df_unpack(x[2], x[3], q[1]);
 }
 
 // 16-byte asynchronous global->shared copy (sm_80+ cp.async, L2 only).
@@ -193,6 +277,24 @@ struct Vec4<double> {
     }
 };
 
+template <>
+struct Vec4<dfl> {
+    static __device__ __forceinline__ void ld(dfl (&v)[4], const dfl *p) {
+        const float4 *q = reinterpret_cast<const float4 *>(p);
+        df_unpack(v[0], v[1], q[0]);
+        df_unpack(v[2], v[3], q[1]);
+    }
+    static __device__ __forceinline__ void ldg(dfl (&v)[4], const dfl *p) {
+        const float4 *q = reinterpret_cast<const float4 *>(p);
+        df_unpack(v[0], v[1], __ldg(q));
+        df_unpack(v[2], v[3], __ldg(q + 1));
+    }
+    static __device__ __forceinline__ void st(dfl *p, const dfl (&v)[4]) {
+        float4 *q = reinterpret_cast<float4 *>(p);
+        q[0] = df_pack(v[0], v[1]);
+        q[1] = df_pack(v[2], v[3]);
+    }
+};
 
 // N = 1, 2 or 4 consecutive elements at p (aligned to N elements): plain load,
 // read-only load and store.
@@ -200,6 +302,8 @@ template <typename T, int N>
 __device__ __forceinline__ void ldn(T (&v)[N], const T *p) {
     if constexpr (N == 4) {
         Vec4<T>::ld(v, p);
+    } else if constexpr (N == 2 && std::is_same_v<T, dfl>) {
+        df_unpack(v[0], v[1], *reinterpret_cast<const float4 *>(p));
     } else if constexpr (N == 2) {
         if constexpr (sizeof(T) == 4) {
             const float2 a = *reinterpret_cast<const float2 *>(p);
@@ -216,6 +320,11 @@ template <typename T, int N>
 __device__ __forceinline__ void ldgn(T (&v)[N], const T *p) {
     if constexpr (N == 4) {
         Vec4<T>::ldg(v, p);
+    } else if constexpr (N == 2 && std::is_same_v<T, dfl>) {
+        df_unpack(v[0], v[1], __ldg(reinterpret_cast<const float4 *>(p)));
+    } else if constexpr (N == 1 && std::is_same_v<T, dfl>) {
+        const float2 a = __ldg(reinterpret_cast<const float2 *>(p));
+        v[0] = dfl(a.x, a.y);
     } else if constexpr (N == 2) {
         if constexpr (sizeof(T) == 4) {
             const float2 a = __ldg(reinterpret_cast<const float2 *>(p));
@@ -232,6 +341,8 @@ template <typename T, int N>
 __device__ __forceinline__ void stn(T *p, const T (&v)[N]) {
     if constexpr (N == 4) {
         Vec4<T>::st(p, v);
+    } else if constexpr (N == 2 && std::is_same_v<T, dfl>) {
+        *reinterpret_cast<float4 *>(p) = df_pack(v[0], v[1]);
     } else if constexpr (N == 2) {
         if constexpr (sizeof(T) == 4)
             *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
@@ -258,6 +369,11 @@ __device__ __forceinline__ int rchunk<double>(int b, int c) {
     return b * 128 + ((c ^ b) & 7) * 16;
 }
 
+template <>
+__device__ __forceinline__ int rchunk<dfl>(int b, int c) {
+    return b * 128 + ((c ^ b) & 7) * 16;
+}
+
 template <typename T>
 __device__ __forceinline__ void r_ld(T (&x)[16], const unsigned char *B, int b);
 template <>
@@ -275,6 +391,13 @@ __device__ __forceinline__ void r_ld<double>(double (&x)[16], const unsigned cha
         const double2 v = *reinterpret_cast<const double2 *>(B + rchunk<double>(b, c));
         x[2 * c] = v.x; x[2 * c + 1] = v.y;
     }
+}
+
+template <>
+__device__ __forceinline__ void r_ld<dfl>(dfl (&x)[16], const unsigned char *B, int b) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        df_unpack(x[2 * c], x[2 * c + 1], *reinterpret_cast<const float4 *>(B + rchunk<dfl>(b, c)));
 }
 
 }  // namespace cheb

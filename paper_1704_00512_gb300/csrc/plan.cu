@@ -28,13 +28,13 @@ static int union_capacity(int64_t nbr, int P, int esz, int nwarps, size_t budget
 }
 
 extern "C" int cheb_tile_count(int32_t precision) {
-    if (precision != CHEB_F64 && precision != CHEB_F32 && precision != CHEB_BF16) return 0;
+    if (precision < CHEB_F64 || precision > CHEB_F64X) return 0;
     return n_tiles(precision);
 }
 
 extern "C" int cheb_tile_info(int32_t precision, int32_t tile, int32_t *panel_width, int32_t *warps,
                               int32_t *blocks_per_sm) {
-    if ((precision != CHEB_F64 && precision != CHEB_F32 && precision != CHEB_BF16) || tile < 0 ||
+    if (precision < CHEB_F64 || precision > CHEB_F64X || tile < 0 ||
         tile >= n_tiles(precision))
         return fail(CHEB_ERR_INVALID, "cheb_tile_info: no tile %d for precision %d", tile, precision);
     const TileCfg c = tile_cfg(precision, tile);
@@ -50,8 +50,8 @@ static int plan_create_impl(const cheb_bsr *P_out, int32_t precision, int32_t ti
     *out = nullptr;
     if (!P_out || P_out->nbr < 1 || P_out->nnzb < P_out->nbr || !P_out->row_ptr || !P_out->col_idx)
         return fail(CHEB_ERR_INVALID, "cheb_plan_create: bad pattern");
-    if (precision != CHEB_F64 && precision != CHEB_F32 && precision != CHEB_BF16)
-        return fail(CHEB_ERR_INVALID, "cheb_plan_create: precision must be CHEB_F64, CHEB_F32 or CHEB_BF16");
+    if (precision < CHEB_F64 || precision > CHEB_F64X)
+        return fail(CHEB_ERR_INVALID, "cheb_plan_create: precision must be CHEB_F64, CHEB_F32, CHEB_BF16 or CHEB_F64X");
     if (P_out->nnzb >= (int64_t)INT32_MAX) return fail(CHEB_ERR_INVALID, "cheb_plan_create: too many blocks");
     if (tile < 0) tile = 0;
     if (tile >= n_tiles(precision)) return fail(CHEB_ERR_INVALID, "cheb_plan_create: no tile %d", tile);
@@ -110,7 +110,7 @@ static int plan_create_impl(const cheb_bsr *P_out, int32_t precision, int32_t ti
     }
     const TileCfg cfg = tile_cfg(precision, tile);
     const int P = cfg.P;
-    const int esz = precision == CHEB_F64 ? 8 : 4;
+    const int esz = (precision == CHEB_F64 || precision == CHEB_F64X) ? 8 : 4;
     plan->tile = tile;
     plan->P = P;
     plan->NW = cfg.NW;
@@ -283,7 +283,32 @@ extern "C" int cheb_plan_col_info(const cheb_plan *plan, int64_t *n_panels, int3
 }
 
 extern "C" int cheb_plan_destroy(cheb_plan *plan) {
+    if (plan) col_free(plan->col);
     delete plan;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_set_gather_builder(cheb_plan *plan, int32_t host) {
+    if (!plan || (host != 0 && host != 1)) return fail(CHEB_ERR_INVALID, "cheb_plan_set_gather_builder: bad arguments");
+    plan->gather_host = host;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_plan_col_lists_copy(const cheb_plan *plan, int32_t which, void *dst, size_t dst_bytes,
+                                        size_t *bytes, void *stream) {
+    if (!plan || !bytes || which < 0 || which > 5)
+        return fail(CHEB_ERR_INVALID, "cheb_plan_col_lists_copy: bad arguments");
+    const ColLists &c = plan->col;
+    if (!c.built || !c.bound) return fail(CHEB_ERR_INVALID, "cheb_plan_col_lists_copy: no bound column-kernel lists");
+    const int64_t np = c.n_panels;
+    const void *src[6] = {c.d_panels, c.d_wchunk, c.d_wrow, c.d_rows, c.d_ent, c.d_slot};
+    const size_t n[6] = {(size_t)np * 16, (size_t)np * (c.NW + 1) * 4, (size_t)np * (c.NW + 1) * 4,
+                         (size_t)c.n_rows * 4, (size_t)c.n_entries * 4, (size_t)c.n_slot * 2};
+    *bytes = n[which];
+    if (!dst) return CHEB_OK;
+    if (dst_bytes < n[which]) return fail(CHEB_ERR_NOSPACE, "cheb_plan_col_lists_copy: %zu < %zu bytes", dst_bytes, n[which]);
+    cudaStream_t s = as_stream(stream);
+    if (n[which]) CHEB_CUDA(cudaMemcpyAsync(dst, src[which], n[which], cudaMemcpyDeviceToDevice, s));
     return CHEB_OK;
 }
 
@@ -399,9 +424,12 @@ extern "C" int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, siz
     // reduced-precision plans: the column-order step kernel's lists (left
     // unbuilt when a panel column or an operator row does not fit it; the
     // per-step products then use the ranking kernel)
+    col_free(plan->col);
     plan->col = ColLists();
-    if (plan->precision != CHEB_F64) {
-        const int rc = col_build(plan, rp, ci, lrp, lci);
+    if (plan->precision == CHEB_F32 || plan->precision == CHEB_BF16) {
+        // the gather-plan kernels (gather.cu) by default; the host threads of
+        // colstep.cu when asked (the same lists, bit for bit)
+        const int rc = plan->gather_host ? col_build(plan, rp, ci, lrp, lci) : col_build_device(plan, L, col_ucap(), s);
         if (rc != CHEB_OK && rc != CHEB_ERR_NOSPACE) return rc;
     }
     plan->op_ws_bytes = plan->lists.bytes() + plan->rlists.bytes() + plan->col.bytes();

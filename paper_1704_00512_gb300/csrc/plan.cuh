@@ -50,12 +50,17 @@ struct ColLists {
     uint32_t *d_rows = nullptr;
     uint32_t *d_ent = nullptr;
     uint16_t *d_slot = nullptr;
+    int64_t n_rows = 0, n_slot = 0;  // row words; P_out blocks (one slot each)
     bool built = false, bound = false;
+    // built by the gather-plan kernels (gather.cu): the d_ arrays live in tmp
+    // (device memory of their own) until cheb_plan_bind_operator copies them
+    bool device = false;
+    void *tmp = nullptr;
     size_t bytes() const {
         if (!built) return 0;
-        return ::cheb::align_up(h_panels.size() * 4) + ::cheb::align_up(h_wchunk.size() * 4) +
-               ::cheb::align_up(h_wrow.size() * 4) + ::cheb::align_up(std::max<size_t>(h_rows.size(), 1) * 4) +
-               ::cheb::align_up(std::max<size_t>(h_ent.size(), 1) * 4) + ::cheb::align_up(h_slot.size() * 2);
+        return ::cheb::align_up((size_t)n_panels * 16) + 2 * ::cheb::align_up((size_t)n_panels * (NW + 1) * 4) +
+               ::cheb::align_up((size_t)std::max<int64_t>(n_rows, 1) * 4) +
+               ::cheb::align_up((size_t)std::max<int64_t>(n_entries, 1) * 4) + ::cheb::align_up((size_t)n_slot * 2);
     }
 };
 
@@ -102,6 +107,7 @@ struct cheb_plan {
     const int32_t *op_ci = nullptr;
     RowLists lists, rlists;
     ColLists col;  // FP32 / BF16 plans: the column-order step kernel's lists
+    int32_t gather_host = 0;  // 1: build them on host threads (the reference builder)
     size_t op_ws_bytes = 0;
     bool op_bound = false;
 };
@@ -225,9 +231,11 @@ constexpr TileCfg TILES_F32[] = {{4, 16, 1}, {4, 8, 1}, {4, 12, 1}, {2, 8, 2}, {
 constexpr TileCfg TILES_F64[] = {{2, 8, 1}, {2, 4, 2}, {1, 8, 2}, {1, 4, 3}, {2, 16, 1}};
 constexpr int N_TILES_F32 = sizeof(TILES_F32) / sizeof(TileCfg);
 constexpr int N_TILES_F64 = sizeof(TILES_F64) / sizeof(TileCfg);
-inline int n_tiles(int precision) { return precision == CHEB_F64 ? N_TILES_F64 : N_TILES_F32; }  // F32 and BF16 share
+// F32 and BF16 share the FP32 shapes, F64X (8-byte double-floats) the FP64 ones
+inline bool wide_elements(int precision) { return precision == CHEB_F64 || precision == CHEB_F64X; }
+inline int n_tiles(int precision) { return wide_elements(precision) ? N_TILES_F64 : N_TILES_F32; }
 inline TileCfg tile_cfg(int precision, int tile) {
-    return precision == CHEB_F64 ? TILES_F64[tile] : TILES_F32[tile];
+    return wide_elements(precision) ? TILES_F64[tile] : TILES_F32[tile];
 }
 // Dynamic shared memory one block may use when MINB blocks share an SM
 // (228 KB per SM, 1 KB reserved per block, a little static shared memory).
@@ -238,8 +246,12 @@ inline size_t smem_budget(int minb) {
 
 // Column-order step kernel (colstep.cu): host build and binding of its lists,
 // and the expansion through it.
+int32_t col_ucap();
 int col_build(cheb_plan *plan, const std::vector<int64_t> &rp, const std::vector<int32_t> &ci,
               const std::vector<int64_t> &lrp, const std::vector<int32_t> &lci);
+// the same lists built by device kernels from the device patterns (gather.cu)
+int col_build_device(cheb_plan *plan, const cheb_bsr *L, int32_t ucap, cudaStream_t s);
+void col_free(ColLists &c);
 int col_bind(ColLists &c, Carve &cv, cudaStream_t s);
 void col_release_host(ColLists &c);
 bool col_usable(const cheb_plan *plan, const cheb_bsr *Mt);

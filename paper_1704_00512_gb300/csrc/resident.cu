@@ -62,6 +62,7 @@ struct ResArgs {
 
 __device__ __forceinline__ float res_round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ double res_round_bf16(double x) { return x; }
+__device__ __forceinline__ dfl res_round_bf16(dfl x) { return x; }
 
 template <typename T>
 __device__ __forceinline__ void r_st(unsigned char *B, int b, const T (&x)[16]);
@@ -75,6 +76,11 @@ template <>
 __device__ __forceinline__ void r_st<double>(unsigned char *B, int b, const double (&x)[16]) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) *reinterpret_cast<double2 *>(B + rchunk<double>(b, c)) = make_double2(x[2 * c], x[2 * c + 1]);
+}
+template <>
+__device__ __forceinline__ void r_st<dfl>(unsigned char *B, int b, const dfl (&x)[16]) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) *reinterpret_cast<float4 *>(B + rchunk<dfl>(b, c)) = df_pack(x[2 * c], x[2 * c + 1]);
 }
 // element i of panel block b
 template <typename T>
@@ -95,6 +101,11 @@ __device__ __forceinline__ void r_row<double>(double (&y)[4], const unsigned cha
     const double2 u = *reinterpret_cast<const double2 *>(B + rchunk<double>(b, 2 * r));
     const double2 v = *reinterpret_cast<const double2 *>(B + rchunk<double>(b, 2 * r + 1));
     y[0] = u.x; y[1] = u.y; y[2] = v.x; y[3] = v.y;
+}
+template <>
+__device__ __forceinline__ void r_row<dfl>(dfl (&y)[4], const unsigned char *B, int b, int r) {
+    df_unpack(y[0], y[1], *reinterpret_cast<const float4 *>(B + rchunk<dfl>(b, 2 * r)));
+    df_unpack(y[2], y[3], *reinterpret_cast<const float4 *>(B + rchunk<dfl>(b, 2 * r + 1)));
 }
 
 // Deterministic thread-block sum of two values, written to dst[0..1] by thread 0.
@@ -304,7 +315,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_resident(const ResArgs<T> a) 
                             for (int m = 0; m < 4; ++m)
 #pragma unroll
                                 for (int c = 0; c < 4; ++c)
-                                    acc[4 * r + c] = fma(h[u][4 * r + m], x[4 * m + c], acc[4 * r + c]);
+                                    acc[4 * r + c] = mac(h[u][4 * r + m], x[4 * m + c], acc[4 * r + c]);
                     }
                     __syncwarp();
                     const int rest = pending - nb;
@@ -319,7 +330,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_resident(const ResArgs<T> a) 
 #pragma unroll
             for (int o = P; o < 32; o <<= 1)
 #pragma unroll
-                for (int i = 0; i < 16; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+                for (int i = 0; i < 16; ++i) acc[i] += shfl_xor_t(acc[i], o);
             // T_{k+1} = 2 (M~ T_k) - T_{k-1}, in place of T_{k-1}, for the panel's blocks only
             if (q < ncols && kg * EPL < 16) {
                 const int e = pos[s * P + q];
@@ -392,6 +403,11 @@ __global__ void k_res_moments(const double *part, int kmax, const int32_t *sys_p
     if (gmom) gmom[(int64_t)sy * mom_stride + k] = g;
 }
 
+__global__ void k_to_dfl_res(const double *in, dfl *out, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = dfl(in[i]);
+}
+
 __global__ void k_to_f32_res(const double *in, float *out, int64_t n, int round_bf16) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = round_bf16 ? __bfloat162float(__float2bfloat16_rn(in[i])) : (float)in[i];
@@ -423,6 +439,17 @@ int run_resident<double>(const cheb_plan *plan, const ResArgs<double> &a, cudaSt
     }
 }
 template <>
+int run_resident<dfl>(const cheb_plan *plan, const ResArgs<dfl> &a, cudaStream_t s) {
+    switch (plan->tile) {
+        CHEB_RES_CASE(dfl, TILES_F64, 0)
+        CHEB_RES_CASE(dfl, TILES_F64, 1)
+        CHEB_RES_CASE(dfl, TILES_F64, 2)
+        CHEB_RES_CASE(dfl, TILES_F64, 3)
+        CHEB_RES_CASE(dfl, TILES_F64, 4)
+        default: return fail(CHEB_ERR_INVALID, "bad FP64 tile %d", plan->tile);
+    }
+}
+template <>
 int run_resident<float>(const cheb_plan *plan, const ResArgs<float> &a, cudaStream_t s) {
     static_assert(N_TILES_F32 == 6, "tile table size");
     switch (plan->tile) {
@@ -439,7 +466,7 @@ int run_resident<float>(const cheb_plan *plan, const ResArgs<float> &a, cudaStre
 
 size_t resident_ws(const cheb_plan *plan, int64_t nnzL, int precision, int kmax) {
     size_t b = 0;
-    if (precision != CHEB_F64) b += align_up(nnzL * BB * 4);
+    if (precision != CHEB_F64) b += align_up(nnzL * BB * (precision == CHEB_F64X ? 8 : 4));
     b += align_up((size_t)plan->n_rpanels * kmax * 2 * sizeof(double));
     return b + 256;
 }
@@ -451,11 +478,18 @@ int resident_impl(const cheb_plan *plan, const cheb_bsr *Mt, int kmax, const int
                   cudaStream_t s, int round_bf16 = 0) {
     Carve cv(ws, ws_bytes);
     const T *Lv;
-    if (sizeof(T) == 8) {
+    const int64_t n = Mt->nnzb * BB;
+    if constexpr (std::is_same_v<T, double>) {
         Lv = reinterpret_cast<const T *>(Mt->vals);
+    } else if constexpr (std::is_same_v<T, dfl>) {
+        dfl *lv = cv.take<dfl>(n);
+        if (!cv.fits()) return fail(CHEB_ERR_NOSPACE, "cheb_expand: workspace too small");
+        k_to_dfl_res<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double *)Mt->vals, lv, n);
+        CHEB_TRY(check_launch("k_to_dfl"));
+        Lv = lv;
     } else {
-        float *lv = cv.take<float>(Mt->nnzb * BB);
-        const int64_t n = Mt->nnzb * BB;
+        float *lv = cv.take<float>(n);
+        if (!cv.fits()) return fail(CHEB_ERR_NOSPACE, "cheb_expand: workspace too small");
         k_to_f32_res<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const double *)Mt->vals, lv, n, round_bf16);
         CHEB_TRY(check_launch("k_to_f32"));
         Lv = reinterpret_cast<const T *>(lv);
@@ -536,6 +570,9 @@ extern "C" int cheb_expand(const cheb_plan *plan, const cheb_bsr *Mt, int32_t n_
     if (precision == CHEB_F64)
         return resident_impl<double>(plan, Mt, n_terms, nullptr, n_terms, cf, nullptr, coeff_stride, n_f, acc, moments,
                                      G, gmoments, n_terms, ws, ws_bytes, s);
+    if (precision == CHEB_F64X)
+        return resident_impl<dfl>(plan, Mt, n_terms, nullptr, n_terms, cf, nullptr, coeff_stride, n_f, acc, moments,
+                                  G, gmoments, n_terms, ws, ws_bytes, s);
     if (precision == CHEB_F32 || precision == CHEB_BF16)
         return resident_impl<float>(plan, Mt, n_terms, nullptr, n_terms, cf, nullptr, coeff_stride, n_f, acc, moments,
                                     G, gmoments, n_terms, ws, ws_bytes, s, precision == CHEB_BF16);
@@ -561,6 +598,9 @@ extern "C" int cheb_expand_batched(const cheb_plan *plan, const cheb_bsr *Mt, in
     if (precision == CHEB_F64)
         return resident_impl<double>(plan, Mt, max_terms, n_terms, 0, cf, n_f > 0 ? coeff_offset : nullptr,
                                      coeff_stride, n_f, acc, moments, G, gmoments, moment_stride, ws, ws_bytes, s);
+    if (precision == CHEB_F64X)
+        return resident_impl<dfl>(plan, Mt, max_terms, n_terms, 0, cf, n_f > 0 ? coeff_offset : nullptr,
+                                  coeff_stride, n_f, acc, moments, G, gmoments, moment_stride, ws, ws_bytes, s);
     if (precision == CHEB_F32 || precision == CHEB_BF16)
         return resident_impl<float>(plan, Mt, max_terms, n_terms, 0, cf, n_f > 0 ? coeff_offset : nullptr,
                                     coeff_stride, n_f, acc, moments, G, gmoments, moment_stride, ws, ws_bytes, s,

@@ -217,7 +217,7 @@ def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FE
     else:
         e0, e1 = bounds_H
     if tol_N is None:
-        tol_N = 1e-9 * N_e if pb.precision == L.F64 else 1e-6 * N_e
+        tol_N = 1e-9 * N_e if pb.precision in (L.F64, L.F64X) else 1e-6 * N_e
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     ws = None
     penalty = []

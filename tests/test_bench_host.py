@@ -15,7 +15,7 @@ from oracle import mlp as omlp  # noqa: E402
 
 def test_workloads_carry_what_their_arm_reads():
     for name, cfg in bench.WORKLOADS.items():
-        assert cfg["precision"] in ("f32", "f64"), name
+        assert cfg["precision"] in ("f32", "f64", "f64x"), name
         if cfg.get("batched"):
             assert {"n_sys", "atoms_lo", "atoms_hi", "r_c", "r_buf", "kT", "tol", "tol_S"} <= set(cfg), name
         elif cfg.get("powers"):
@@ -73,3 +73,10 @@ def test_shipped_proposal_weights_match_the_network():
     out, _ = omlp.forward(theta.astype(np.float64), X[:8].astype(np.float64))
     assert out.shape == (8, 2) and np.all(np.isfinite(out))
     assert X.shape[1] == omlp.N_IN and len(xstar) == len(scale) == len(X)
+
+
+def test_traffic_scales_with_blocks_and_is_tied_to_the_measured_source():
+    t = bench.col_traffic_per_launch("mu4", 4, [100, 200], bench.COL_TRAFFIC["blocks_P_out"] * 2)
+    want = 2 * (bench.COL_TRAFFIC["pass1_bytes"] * 100 + bench.COL_TRAFFIC["pass2_4acc_bytes"] * 200) / 300
+    assert t == int(want)
+    assert bench.col_traffic_per_launch("twopass", 1, [100, 100], 10) is None
