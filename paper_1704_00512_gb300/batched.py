@@ -38,6 +38,7 @@ import numpy as np
 import torch
 
 from . import _lib as L
+from . import solve
 
 
 def _slice_bsr(pattern: L.Bsr, vals: torch.Tensor, b0: int) -> L.Bsr:
@@ -152,11 +153,12 @@ def _pack_coeffs(funcs_per_sys, bounds, n_terms, device) -> tuple[torch.Tensor, 
 
 
 def prepare_batched(bp: BatchedProblem, kT, tol: float = 1e-7, tol_S: float = 1e-10, kind: int = L.FERMI,
-                    lanczos_k: int = 40, n_max: int = 16384) -> dict:
+                    lanczos_k: int = 40, n_max: int = 16384, bounds_H=None) -> dict:
     """Steps 2-3 of the module docstring: S^-1/2, H~', per-system bounds and degrees, G.
 
     kT: one smearing for every system, or a list with one per system (it sets
-    each system's degree)."""
+    each system's degree).  bounds_H: per-system bounds of H' to use instead of
+    Lanczos (a warm start, e.g. the previous step's; None entries run Lanczos)."""
     dev = bp.device
     nsys = bp.nsys
     kTs = list(kT) if isinstance(kT, (list, tuple, np.ndarray)) else [kT] * nsys
@@ -184,7 +186,10 @@ def prepare_batched(bp: BatchedProblem, kT, tol: float = 1e-7, tol_S: float = 1e
     Hpt = torch.empty_like(Hp_vals)
     for i in range(nsys):
         Hi = _slice_bsr(bp.PH[i], Hp_vals, bp.hoff[i])
-        e0, e1, _ = L.bounds(Hi, lanczos_k)
+        if bounds_H is not None and bounds_H[i] is not None:
+            e0, e1 = bounds_H[i]
+        else:
+            e0, e1, _ = L.bounds(Hi, lanczos_k)
         bH.append((e0, e1))
         L.scale(Hi, e0, e1, out=Hpt[bp.hoff[i]:bp.hoff[i + 1]])
         nH.append(L.coeffs([{"kind": kind, "mu": 0.5 * (e0 + e1), "kT": kTs[i]}], e0, e1, tol, n_max,
@@ -199,13 +204,21 @@ def prepare_batched(bp: BatchedProblem, kT, tol: float = 1e-7, tol_S: float = 1e
 
 def foe_batched(bp: BatchedProblem, kT: float, N_e: list[float], tol: float = 1e-7, tol_S: float = 1e-10,
                 kind: int = L.FERMI, lanczos_k: int = 40, n_max: int = 16384, max_iter: int = 100,
-                tol_N: list[float] | None = None, use_graphs: bool = True, timings: dict | None = None) -> dict:
-    """Density matrices of every system of the batch (see the module docstring)."""
+                tol_N: list[float] | None = None, use_graphs: bool = True, bounds_H=None,
+                penalty_alpha: float = -200.0, penalty_threshold: float = 1.0, penalty_terms: int = 512,
+                timings: dict | None = None) -> dict:
+    """Density matrices of every system of the batch (see the module docstring).
+
+    Pass 1 also collects every system's Tr T_k; the penalty check of Eq. 5 runs
+    on them before the bisections, and a system whose spectrum leaves its bounds
+    raises ChebError(ERR_BOUNDS) naming the system and the bound (the plain
+    solve.foe widens and retries; a batch shares its passes).  bounds_H: as in
+    prepare_batched."""
     tm = {} if timings is None else timings
     dev = bp.device
     t0 = time.perf_counter()
     nsys = bp.nsys
-    pr = prepare_batched(bp, kT, tol, tol_S, kind, lanczos_k, n_max)
+    pr = prepare_batched(bp, kT, tol, tol_S, kind, lanczos_k, n_max, bounds_H)
     A, Hpt, G, bS, nS, bH, nH = (pr[k] for k in ("A", "Hpt", "G", "bounds_S", "n_S", "bounds_H", "n_terms"))
     torch.cuda.synchronize(dev)
     tm["setup_s"] = time.perf_counter() - t0
@@ -219,6 +232,7 @@ def foe_batched(bp: BatchedProblem, kT: float, N_e: list[float], tol: float = 1e
         st = {"nt": torch.as_tensor(nH, dtype=torch.int32, device=dev),
               "Hpt": Hpt.vals.clone(), "A": A.clone(), "G": G.clone(),
               "g": torch.zeros((nsys, kmax), dtype=torch.float64, device=dev),
+              "t": torch.zeros((nsys, kmax), dtype=torch.float64, device=dev),
               "res": torch.zeros((nsys, 48), dtype=torch.uint8, device=dev),
               "mws": [L._ws(8 * n, dev) for n in nH],
               "c": torch.zeros(int(sum(nH)), dtype=torch.float64, device=dev),
@@ -245,8 +259,17 @@ def foe_batched(bp: BatchedProblem, kT: float, N_e: list[float], tol: float = 1e
     # kT and N_e as kernel arguments, which change with H, so it runs outside.
     def pass1():
         st["g"].zero_()
-        L.expand_batched(st["planX"], Hst, kmax, st["nt"], None, None, 0, [], G=st["G"], gmoments=st["g"],
-                         moment_stride=kmax, precision=bp.precision, ws=st["wsA"])
+        st["t"].zero_()
+        L.expand_batched(st["planX"], Hst, kmax, st["nt"], None, None, 0, [], moments=st["t"], G=st["G"],
+                         gmoments=st["g"], moment_stride=kmax, precision=bp.precision, ws=st["wsA"])
+
+    def check_bounds():
+        for i in range(nsys):
+            verdict, value = solve.penalty(st["t"][i], nH[i], penalty_alpha, penalty_threshold, penalty_terms)
+            if verdict != 0:
+                side = {-1: "lower", 1: "upper"}.get(verdict, "a")
+                raise L.ChebError(L.ERR_BOUNDS, f"penalty check (Eq. 5): system {i} leaves its {side} bound "
+                                                f"(trace {value:g} on [{bH[i][0]}, {bH[i][1]}])")
 
     def searches():
         for i in range(nsys):
@@ -270,6 +293,7 @@ def foe_batched(bp: BatchedProblem, kT: float, N_e: list[float], tol: float = 1e
         ev[0].record()
         pass1()
         ev[1].record()
+        check_bounds()
         searches()
         res = L.decode_mu_batch(st["res"])
         mus = [r["mu"] for r in res]
@@ -290,6 +314,7 @@ def foe_batched(bp: BatchedProblem, kT: float, N_e: list[float], tol: float = 1e
         ev[0].record()
         gA.replay()
         ev[1].record()
+        check_bounds()
         searches()
         res = L.decode_mu_batch(st["res"])
         mus = [r["mu"] for r in res]
@@ -301,6 +326,7 @@ def foe_batched(bp: BatchedProblem, kT: float, N_e: list[float], tol: float = 1e
         ev[0].record()
         pass1()
         ev[1].record()
+        check_bounds()
         searches()
         res = L.decode_mu_batch(st["res"])
         mus = [r["mu"] for r in res]

@@ -43,14 +43,15 @@ class Instance:
 
 
 def prepare(pb: solve.Problem, tol_S: float = 1e-10, lanczos_k: int = 40):
-    """S^-1/2, H', bounds of H', scaled H~' and the trace functional G (as in solve.foe)."""
+    """S^-1/2, H', bounds of H', scaled H~', the trace functional G (as in
+    solve.foe) and H' itself (to rescale if the penalty check moves a bound)."""
     pw = solve.powers(pb, exponents=(-0.5,), tol=tol_S, precision=L.F64)
     A = pw["acc"][0]
     Hp = solve.orthogonalise(pb, A)
     e0, e1, _ = L.bounds(Hp, lanczos_k)
     Hpt = Hp.with_vals(L.scale(Hp, e0, e1))
     G = solve.trace_functional(pb, A)
-    return A, Hpt, (e0, e1), G
+    return A, Hpt, (e0, e1), G, Hp
 
 
 def moments32(pb: solve.Problem, Hpt: L.Bsr, stepwise: bool = False) -> torch.Tensor:
@@ -69,7 +70,7 @@ def label_instance(sysm, r_buf: float, kT: float, N_e: float, device, tol: float
                    precision: int = L.F32) -> Instance:
     """Features and the bisection's mu* (the label) for one generated system."""
     pb = solve.problem_from_system(sysm, r_buf, device, precision)
-    A, Hpt, (e0, e1), G = prepare(pb)
+    A, Hpt, (e0, e1), G, _ = prepare(pb)
     n, _ = L.coeffs([{"kind": L.FERMI, "mu": 0.5 * (e0 + e1), "kT": kT}], e0, e1, tol, 16384, device=pb.device)
     t = torch.zeros(n, dtype=torch.float64, device=pb.device)
     g = torch.zeros(n, dtype=torch.float64, device=pb.device)
@@ -161,14 +162,22 @@ def load_proposal(device, path: str = WEIGHTS) -> Proposal:
 def foe_learned(pb: solve.Problem, prop: Proposal, kT: float, N_e: float, tol: float = 1e-7, n_mu: int = 8,
                 min_half_kT: float = 0.05, max_half_kT: float = 1.0, tol_N: float | None = None,
                 prepared=None, bracket: tuple[float, float] | None = None, stepwise: bool = True,
-                timings: dict | None = None) -> dict:
+                penalty_alpha: float = -200.0, penalty_threshold: float = 1.0, penalty_widen: float = 0.05,
+                penalty_terms: int = 512, timings: dict | None = None, _checks=None) -> dict:
     """One-expansion FOE with the learned bracket; bisection judges, fallback on a miss.
 
     With n_mu = 8 Chebyshev nodes the interpolation error of the Fermi function
     in mu stays below 4e-7 for a half-width of one kT and below 2e-9 for half a
-    kT.  bracket: (mu_hat, half) to use instead of the network's (tests)."""
+    kT.  bracket: (mu_hat, half) to use instead of the network's (tests).
+    prepared: (A, H~', bounds, G[, H']) from prepare().  The pass also collects
+    Tr T_k for the penalty check of Eq. 5: a failing bound is widened by
+    penalty_widen of the interval and the solve repeated once (this needs H'
+    in prepared); a second failure raises ChebError(ERR_BOUNDS)."""
     tm = {} if timings is None else timings
-    A, Hpt, (e0, e1), G = prepare(pb) if prepared is None else prepared
+    checks = [] if _checks is None else _checks
+    prepared = prepare(pb) if prepared is None else prepared
+    A, Hpt, (e0, e1), G = prepared[:4]
+    Hp = prepared[4] if len(prepared) > 4 else None
     sigma, tau = 2.0 / (e1 - e0), 0.5 * (e0 + e1)
     if bracket is None:
         t32 = moments32(pb, Hpt, stepwise=stepwise)
@@ -185,10 +194,21 @@ def foe_learned(pb: solve.Problem, prop: Proposal, kT: float, N_e: float, tol: f
     _, c = L.coeffs([{"kind": L.FERMI, "mu": m, "kT": kT} for m in mus], e0, e1, 0.0, n, device=pb.device)
     accs = [pb.zeros_out() for _ in mus]
     g = torch.zeros(n, dtype=torch.float64, device=pb.device)
+    t = torch.zeros(n, dtype=torch.float64, device=pb.device)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
-    ws = L.expand(pb.planX, Hpt, n, c, accs, G=G, gmoments=g, precision=pb.precision, stepwise=stepwise)
+    ws = L.expand(pb.planX, Hpt, n, c, accs, moments=t, G=G, gmoments=g, precision=pb.precision,
+                  stepwise=stepwise)
     ev[1].record()
+    verdict, value = solve.penalty(t, n, penalty_alpha, penalty_threshold, penalty_terms)
+    checks.append((verdict, value, (e0, e1)))
+    if verdict != 0:
+        if len(checks) > 1 or Hp is None:
+            raise L.ChebError(L.ERR_BOUNDS, f"penalty check (Eq. 5) failed: trace {value:g} on [{e0}, {e1}]")
+        b = solve.widen((e0, e1), verdict, penalty_widen)
+        return foe_learned(pb, prop, kT, N_e, tol, n_mu, min_half_kT, max_half_kT, tol_N,
+                           (A, Hp.with_vals(L.scale(Hp, *b)), b, G, Hp), bracket, stepwise, penalty_alpha,
+                           penalty_threshold, penalty_widen, penalty_terms, timings, checks)
     if tol_N is None:
         tol_N = 1e-6 * N_e
     r = L.decode_mu_result(L.mu_search(g, n, e0, e1, L.FERMI, kT, N_e, tol_N))
@@ -206,5 +226,5 @@ def foe_learned(pb: solve.Problem, prop: Proposal, kT: float, N_e: float, tol: f
     F = solve.postprocess(pb, A, p)
     trFS = L.trace(pb.P_out.with_vals(F), pb.S)
     tm["events"] = ev
-    return {"F": F, "p": p, "mu": mu, "mu_hat": mu_hat, "half": half, "passes": passes, "n_terms": n,
-            "mu_result": r, "trace_FS": trFS, "bounds_H": (e0, e1), "n_mu": n_mu}
+    return {"F": F, "p": p, "mu": mu, "mu_hat": mu_hat, "half": half, "passes": passes + len(checks) - 1,
+            "n_terms": n, "mu_result": r, "trace_FS": trFS, "bounds_H": (e0, e1), "n_mu": n_mu, "penalty": checks}

@@ -180,6 +180,27 @@ def overlap_setup(pb: Problem, tol_S: float = 1e-10, lanczos_k: int = 40, bounds
     return {"A": A, "G": G, "bounds_S": pw["bounds"], "n_S": pw["n_terms"]}
 
 
+def penalty(t: torch.Tensor, m: int, alpha: float = -200.0, threshold: float = 1.0, terms: int = 512):
+    """Eq. 5 on the first min(m, terms) traces t_k = Tr T_k of an expansion:
+    (verdict, value), verdict 0 when the spectrum lies in the bounds, -1 / +1
+    for the lower / upper bound, 2 for a non-finite trace.  |alpha| (scaled
+    variable) is capped at 2/5 of the terms, so that the penalty polynomial
+    resolves it."""
+    npen = min(m, terms)
+    return L.penalty_check(t, npen, -min(abs(alpha), 0.4 * npen), threshold)
+
+
+def widen(bounds: tuple[float, float], verdict: int, frac: float) -> tuple[float, float]:
+    """The bound the penalty verdict names, moved out by frac of the interval width."""
+    e0, e1 = bounds
+    w = frac * (e1 - e0)
+    if verdict in (-1, 2):
+        e0 -= w
+    if verdict in (1, 2):
+        e1 += w
+    return e0, e1
+
+
 def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FERMI, n_max: int = 16384,
         lanczos_k: int = 40, tol_N: float | None = None, bounds_S=None, n_S=None, bounds_H=None, n_H=None,
         max_iter: int = 100, form: str = "twopass", n_mu: int = 4, mu_half_kT: float = 0.02,
@@ -220,7 +241,7 @@ def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FE
         tol_N = 1e-9 * N_e if pb.precision in (L.F64, L.F64X) else 1e-6 * N_e
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     ws = None
-    penalty = []
+    checks = []
     for attempt in range(2):
         Hpt = Hp.with_vals(L.scale(Hp, e0, e1))
         if n_H is None:
@@ -235,19 +256,13 @@ def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FE
         ws = L.expand(pb.planX, Hpt, m, None, [], moments=t, G=G, gmoments=g, precision=pb.precision, ws=ws,
                       stepwise=stepwise)
         ev[1].record()
-        npen = min(m, penalty_terms)
-        alpha = -min(abs(penalty_alpha), 0.4 * npen)
-        verdict, value = L.penalty_check(t, npen, alpha, penalty_threshold)
-        penalty.append((verdict, value, (e0, e1)))
+        verdict, value = penalty(t, m, penalty_alpha, penalty_threshold, penalty_terms)
+        checks.append((verdict, value, (e0, e1)))
         if verdict == 0:
             break
         if attempt == 1:
             raise L.ChebError(L.ERR_BOUNDS, f"penalty check (Eq. 5) failed twice: trace {value:g} on [{e0}, {e1}]")
-        w = penalty_widen * (e1 - e0)
-        if verdict in (-1, 2):
-            e0 -= w
-        if verdict in (1, 2):
-            e1 += w
+        e0, e1 = widen((e0, e1), verdict, penalty_widen)
     passes = 1
     em = None
     if form == "twopass":
@@ -290,7 +305,7 @@ def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FE
     tm["form"] = form
     return {"F": F, "p": p, "mus": mus, "A": A, "Hp": Hp, "G": G, "mu": mu, "mu_result": r, "mu_half": r_half,
             "moments": t, "gmoments": gm, "n_terms": n, "n_pass1": m, "passes": passes, "bounds_H": (e0, e1),
-            "bounds_S": ov["bounds_S"], "n_S": ov["n_S"], "trace_FS": trFS, "penalty": penalty,
+            "bounds_S": ov["bounds_S"], "n_S": ov["n_S"], "trace_FS": trFS, "penalty": checks,
             "emoments": em, "G_H": GH, "kT": kT, "kind": kind, "N_e": N_e, "tol_N": tol_N}
 
 

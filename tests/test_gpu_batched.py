@@ -112,3 +112,22 @@ def test_autotune_caches_a_valid_tile():
     t = batched.autotune_tile(bp.P_out, bp.starts, cg.F32, Ht)
     assert 0 <= t < len(cg.tile_shapes(cg.F32))
     assert batched.autotune_tile(bp.P_out, bp.starts, cg.F32, Ht) == t
+
+
+def test_batched_penalty_flags_the_system_whose_bound_is_shrunk():
+    # Eq. 5 on every system's own traces from pass 1: Lanczos bounds pass; a
+    # shrunk upper bound of system 2 (given as a warm start) is reported as
+    # CHEB_ERR_BOUNDS naming that system and bound
+    systems = _systems()
+    N_e = [2.0 * s.n_atoms for s in systems]
+    bp = batched.BatchedProblem(systems, R_BUF, DEV, precision=cg.F64)
+    out = batched.foe_batched(bp, KT, N_e, tol=1e-9, tol_S=1e-10, use_graphs=False)
+    bH = list(out["bounds_H"])
+    e0, e1 = bH[2]
+    bH[2] = (e0, e1 - 0.02 * (e1 - e0))
+    with pytest.raises(cg.ChebError) as e:
+        batched.foe_batched(bp, KT, N_e, tol=1e-9, tol_S=1e-10, use_graphs=False, bounds_H=bH)
+    assert e.value.code == batched.L.ERR_BOUNDS and "system 2" in str(e.value) and "upper" in str(e.value)
+    # the warm start with the Lanczos bounds themselves solves as before
+    again = batched.foe_batched(bp, KT, N_e, tol=1e-9, tol_S=1e-10, use_graphs=False, bounds_H=out["bounds_H"])
+    assert relF(again["F"].cpu().numpy(), out["F"].cpu().numpy()) < 1e-12

@@ -151,3 +151,35 @@ def test_one_pass_form_at_the_bench_degree_within_target_of_fp64():
         assert out["n_terms"] >= 7000
         assert err < 1e-6
         assert abs(out["trace_FS"].item() - N_e) < 1e-6 * N_e
+
+
+@pytest.mark.parametrize("side", ["lower", "upper"])
+def test_learned_solve_penalty_widens_a_shrunk_bound(side):
+    # Eq. 5 on the one-pass form: a shrunk bound fails the check on the pass's
+    # own traces, the bound is widened and the solve repeated; the result
+    # matches the solve on Lanczos bounds
+    s = synth.make_system(52, 3.5, 521)
+    kT = 0.05
+    N_e = float(s.n_rows // 2)
+    pb = solve.problem_from_system(s, 1.5, DEV, cg.F64)
+    A, Hpt, (e0, e1), G, Hp = learned.prepare(pb)
+    prop = learned.Proposal(np.zeros(omlp.N_PARAMS), DEV)  # unused: the bracket is given
+    good = learned.foe_learned(pb, prop, kT, N_e, tol=1e-9, tol_N=1e-9 * N_e, prepared=(A, Hpt, (e0, e1), G, Hp))
+    br = (good["mu"], 0.5 * kT)
+    good = learned.foe_learned(pb, prop, kT, N_e, tol=1e-9, tol_N=1e-9 * N_e, prepared=(A, Hpt, (e0, e1), G, Hp),
+                               bracket=br)
+    assert [c[0] for c in good["penalty"]] == [0]
+    w = e1 - e0
+    b = (e0 + 0.02 * w, e1) if side == "lower" else (e0, e1 - 0.02 * w)
+    out = learned.foe_learned(pb, prop, kT, N_e, tol=1e-9, tol_N=1e-9 * N_e,
+                              prepared=(A, Hp.with_vals(cg.scale(Hp, *b)), b, G, Hp), bracket=br)
+    assert [c[0] for c in out["penalty"]] == [-1 if side == "lower" else 1, 0]
+    assert out["passes"] >= 2
+    assert abs(out["mu"] - good["mu"]) < 1e-6
+    F, Fg = out["F"].cpu().numpy(), good["F"].cpu().numpy()
+    assert np.linalg.norm(F - Fg) / np.linalg.norm(Fg) < 1e-6
+    # without H' to rescale, the failing check is an error
+    with pytest.raises(cg.ChebError) as e:
+        learned.foe_learned(pb, prop, kT, N_e, tol=1e-9, tol_N=1e-9 * N_e,
+                            prepared=(A, Hp.with_vals(cg.scale(Hp, *b)), b, G), bracket=br)
+    assert e.value.code == learned.L.ERR_BOUNDS
