@@ -536,6 +536,38 @@ int cheb_mlp_adam(float *theta, const float *grad, float *m, float *v, int32_t t
 int cheb_mlp_features(const double *moments, int64_t n_rows, double emin, double emax, double N_e,
                       float *features, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Segment Storage Format (Sec. "Storage format of the sparse matrices"), for
+ * callers that hold matrices that way: the nonzeros of the n x n scalar matrix
+ * in one value array; the pattern as nseg segments of consecutive entries,
+ * keyg[4 s .. 4 s + 3] = (c_s, c_e, r_s, r_e), the first and last column and
+ * row of segment s (the (2,2,nseg) descriptor in first-index-fastest order),
+ * and keyv[s], the position in the value array where it starts; all indices
+ * 1-based.  A segment covers the entries from (r_s, c_s) to (r_e, c_e) in
+ * row-major order.
+ *   export_size (host-returning): the segment and value counts of the scalar
+ *     pattern of A (every entry of a present 4x4 block): one segment per scalar
+ *     row and maximal run of consecutive block columns; nnz = 16 nnzb.
+ *   export: keyg (device int32[4 nseg]), keyv (device int64[nseg]) and vals
+ *     (device double[nnz], row-major) of A (FP64); nseg must be export_size's.
+ *     Asynchronous.
+ *   import_pattern (host-returning): the 4x4 block pattern holding every entry
+ *     of the segments keyg (HOST int32[4 nseg]) of an n x n matrix (n a
+ *     multiple of 4) plus every diagonal block: *nnzb; with row_ptr (device
+ *     int64[n/4 + 1]) and col_idx (device int32[nnzb]) also the pattern.
+ *   import_values (host-returning): A (a pattern from import_pattern, FP64
+ *     vals written) = the matrix of keyg, keyv (device) and vals (device
+ *     double[nvals]), zero outside the segments.
+ * Errors: CHEB_ERR_INVALID for bad sizes, a segment outside the matrix or its
+ * values outside vals, or an entry outside A's pattern.
+ */
+int cheb_ssf_export_size(const cheb_bsr *A, int64_t *nseg, int64_t *nnz, void *stream);
+int cheb_ssf_export(const cheb_bsr *A, int64_t nseg, int32_t *keyg, int64_t *keyv, double *vals, void *stream);
+int cheb_ssf_import_pattern(int64_t n, int64_t nseg, const int32_t *keyg, int64_t *nnzb, int64_t *row_ptr,
+                            int32_t *col_idx, void *stream);
+int cheb_ssf_import_values(const cheb_bsr *A, int64_t nseg, const int32_t *keyg, const int64_t *keyv,
+                           const double *vals, int64_t nvals, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

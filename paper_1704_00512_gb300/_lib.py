@@ -12,6 +12,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -35,6 +36,7 @@ EXPORTS = [
     "cheb_penalty_trace", "cheb_mu_search", "cheb_mu_search_noalloc", "cheb_newton_schulz", "cheb_newton_schulz_isqrt",
     "cheb_plan_col_info", "cheb_penalty_check", "cheb_mu_nodes", "cheb_lagrange_weights", "cheb_bounds_spd",
     "cheb_series_value", "cheb_bounds_warm", "cheb_plan_set_gather_builder", "cheb_plan_col_lists_copy",
+    "cheb_ssf_export_size", "cheb_ssf_export", "cheb_ssf_import_pattern", "cheb_ssf_import_values",
 ]
 
 
@@ -97,6 +99,10 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
         "cheb_mu_nodes": ([dbl, dbl, i32, P(dbl)], i32),
         "cheb_series_value": ([p, p, i32, p, p], i32),
         "cheb_plan_set_gather_builder": ([p, i32], i32),
+        "cheb_ssf_export_size": ([P(CBsr), P(i64), P(i64), p], i32),
+        "cheb_ssf_export": ([P(CBsr), i64, p, p, p, p], i32),
+        "cheb_ssf_import_pattern": ([i64, i64, p, P(i64), p, p, p], i32),
+        "cheb_ssf_import_values": ([P(CBsr), i64, p, p, p, i64, p], i32),
         "cheb_plan_col_lists_copy": ([p, i32, p, ctypes.c_size_t, P(ctypes.c_size_t), p], i32),
         "cheb_bounds_warm": ([P(CBsr), i32, p, dbl, P(dbl), P(dbl), P(dbl), P(dbl), p, ctypes.c_size_t, p], i32),
         "cheb_lagrange_weights": ([P(dbl), i32, dbl, P(dbl)], i32),
@@ -398,6 +404,43 @@ def plan_col_lists(plan: Plan, stream=None) -> list[torch.Tensor]:
         _check(lib.cheb_plan_col_lists_copy(plan.handle, which, _ptr(t), t.numel(), ctypes.byref(nb), _stream(stream)))
         out.append(t[:nb.value])
     return out
+
+
+def ssf_export(A: Bsr, stream=None):
+    """cheb_ssf_export: (keyg int32 [nseg, 4] as (c_s, c_e, r_s, r_e), keyv int64 [nseg], vals) on the device."""
+    lib = load()
+    cb = A.c()
+    nseg, nnz = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib.cheb_ssf_export_size(ctypes.byref(cb), ctypes.byref(nseg), ctypes.byref(nnz), _stream(stream)))
+    dev = A.vals.device
+    keyg = torch.empty((max(nseg.value, 1), 4), dtype=torch.int32, device=dev)
+    keyv = torch.empty(max(nseg.value, 1), dtype=torch.int64, device=dev)
+    vals = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=dev)
+    _check(lib.cheb_ssf_export(ctypes.byref(cb), nseg.value, _ptr(keyg), _ptr(keyv), _ptr(vals), _stream(stream)))
+    return keyg[:nseg.value], keyv[:nseg.value], vals[:nnz.value]
+
+
+def ssf_import(n: int, keyg, keyv: torch.Tensor, vals: torch.Tensor, stream=None) -> Bsr:
+    """cheb_ssf_import_pattern + cheb_ssf_import_values: the 4x4 block-CSR matrix of SSF descriptors.
+    keyg: host or device int32 [nseg, 4]; keyv, vals: device tensors."""
+    lib = load()
+    kg_host = np.ascontiguousarray(torch.as_tensor(keyg).cpu().numpy().astype(np.int32)).reshape(-1)
+    nseg = kg_host.size // 4
+    nnzb = ctypes.c_int64(0)
+    kgp = kg_host.ctypes.data_as(ctypes.c_void_p)
+    _check(lib.cheb_ssf_import_pattern(n, nseg, kgp, ctypes.byref(nnzb), None, None, _stream(stream)))
+    dev = vals.device
+    rp = torch.empty(n // 4 + 1, dtype=torch.int64, device=dev)
+    ci = torch.empty(max(nnzb.value, 1), dtype=torch.int32, device=dev)
+    _check(lib.cheb_ssf_import_pattern(n, nseg, kgp, ctypes.byref(nnzb), _ptr(rp), _ptr(ci), _stream(stream)))
+    A = Bsr(rp, ci[:nnzb.value], torch.empty((nnzb.value, 4, 4), dtype=torch.float64, device=dev))
+    kg_dev = torch.as_tensor(kg_host, device=dev)
+    kv = keyv.to(device=dev, dtype=torch.int64).contiguous()
+    vv = vals.to(device=dev, dtype=torch.float64).contiguous()
+    cb = A.c()
+    _check(lib.cheb_ssf_import_values(ctypes.byref(cb), nseg, _ptr(kg_dev), _ptr(kv), _ptr(vv), vv.numel(),
+                                      _stream(stream)))
+    return A
 
 
 def plan_resident_info(plan: Plan) -> tuple[int, int, int]:

@@ -7,6 +7,8 @@ expansion is checked element by element on those columns at full size:
     system (r_c 10, r_buf 4 bohr) with a 9,216-term Fermi expansion (the
     bench's kT = 0.005 Ha scaled to this operator's spectral width): relative
     Frobenius error of the accumulator over 64 sampled columns below 1e-6;
+    the BF16 mode's error on the same columns (reported; bounded by the FP32
+    error times the ratio of unit roundoffs);
   * FP64 products at the same term count on a 1,000-atom system (32 sampled
     columns): below 1e-10;
   * unions near the shared-memory cap (3,000 atoms, 14 bohr output cutoff),
@@ -78,6 +80,13 @@ def test_fp32_expansion_at_the_bench_configuration():
     err = relF_cols(acc[0], want[0], P_out, cols)
     print(f"FP32, 9216 terms, 40,000 rows: relative Frobenius error over 64 sampled columns {err:.3e}")
     assert err < 1e-6
+    # BF16 mode on the same operator and columns: every stored T_k rounded to
+    # bfloat16 (unit roundoff 2^-8 instead of 2^-24).  Its error is reported;
+    # the bar is the FP32 error scaled by the ratio of unit roundoffs (x 4).
+    _, acc16 = gpu_expand(H, P_out, lo, hi, c, cg.BF16)
+    err16 = relF_cols(acc16[0], want[0], P_out, cols)
+    print(f"BF16, 9216 terms, 40,000 rows: relative Frobenius error over 64 sampled columns {err16:.3e}")
+    assert err < err16 < 4 * 2.0 ** 16 * err
 
 
 def test_fp64_expansion_at_the_bench_term_count():
