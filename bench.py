@@ -569,8 +569,9 @@ def run_powers(args, rank: int, world: int, local: int):
                    "triples": triples, "l2": "inputs larger than L2 (no flush)"},
         "roofline": roof,
         "vs_fp64_dfma": vs_dfma,
-        "e2e": {"value": round(job_throughput(args.e2e_steps, world, te_ms), 4), "unit": UNIT,
-                "h2d_bytes_per_step": int(h_S.numel() * 8), "d2h_bytes_per_step": int(sum(h.numel() for h in h_out) * 8)},
+        "e2e": None if args.e2e_steps == 0 else {
+            "value": round(job_throughput(args.e2e_steps, world, te_ms), 4), "unit": UNIT,
+            "h2d_bytes_per_step": int(h_S.numel() * 8), "d2h_bytes_per_step": int(sum(h.numel() for h in h_out) * 8)},
         "gpu_launches": int(launches), "clocks": clocks,
     }
     if world > 1:

@@ -187,17 +187,31 @@ int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, size_t *op_ws_
  * fewest chunks so far, and the entry streams; a few scalars and per-panel
  * maxima come back to the host to size the lists).  It uses device memory of
  * its own until cheb_plan_bind_operator copies the lists into the operator
- * workspace.  cheb_plan_set_gather_builder(plan, 1), before attaching, builds
- * the same lists on host threads instead (the reference builder; the two are
- * bit-identical).  cheb_plan_col_lists_copy copies bound list `which` (0
- * panels int32[4 per panel], 1 warp chunk starts and 2 warp row starts
- * int32[panels][17], 3 row words, 4 entry words uint32, 5 slots uint16[nnzb])
- * into device memory dst (dst_bytes); *bytes receives its size (dst NULL: size
- * only).  Asynchronous. */
+ * workspace.
+ *
+ * Builders.  By default cheb_plan_create and cheb_plan_attach_operator build
+ * everything with device kernels from the device arrays (pattern checks, the
+ * transposition map, the panel walks, the operator row lists of both panel
+ * sets and the column kernel's lists); only the panel tables -- a few integers
+ * per panel -- and sizes come back to the host, and cheb_plan_attach_operator
+ * then needs a bound plan.  cheb_set_plan_builder(1) makes later plans use the
+ * host threads instead (a copy of the patterns on the host: the reference
+ * builders, bit-identical), cheb_set_plan_builder(0) restores the device;
+ * cheb_plan_set_gather_builder(plan, host) picks the builder of one plan's
+ * next attach.  cheb_plan_lists_copy copies bound table `which` into device
+ * memory dst (dst_bytes); *bytes receives its size (dst NULL: size only):
+ * 0 column-kernel panels int32[4 per panel], 1 its warp chunk starts and 2
+ * warp row starts int32[panels][17], 3 row words, 4 entry words uint32, 5
+ * slots uint16[nnzb]; 6 the transposition map int32[nnzb]; 7 step panels and
+ * 8 resident panels int32[2 per panel]; 9 the system of each resident panel,
+ * 10 the first resident panel of each system (+ end); 11-13 the step panels'
+ * operator row lists (first row pointer per panel int64, row pointers int32,
+ * entries uint32), 14-16 the resident panels' ones.  Asynchronous. */
 int cheb_plan_col_info(const cheb_plan *plan, int64_t *n_panels, int32_t *max_union, int64_t *n_entries);
+int cheb_set_plan_builder(int32_t host);
 int cheb_plan_set_gather_builder(cheb_plan *plan, int32_t host);
-int cheb_plan_col_lists_copy(const cheb_plan *plan, int32_t which, void *dst, size_t dst_bytes, size_t *bytes,
-                             void *stream);
+int cheb_plan_lists_copy(const cheb_plan *plan, int32_t which, void *dst, size_t dst_bytes, size_t *bytes,
+                         void *stream);
 int cheb_plan_bind_operator(cheb_plan *plan, void *op_ws, size_t op_ws_bytes, void *stream);
 int cheb_plan_destroy(cheb_plan *plan);
 

@@ -521,7 +521,9 @@ def lanczos(A: Bsr, v0: np.ndarray, k: int) -> tuple[np.ndarray, np.ndarray]:
         w = w - a * v
         b = float(np.linalg.norm(w))
         alpha[j], beta[j] = a, b
-        if b == 0.0:
+        # breakdown (reading: beta at rounding level of the step's scale, 1e-12
+        # of |alpha_j| + beta_{j-1}): the Krylov space is invariant
+        if b == 0.0 or b <= 1e-12 * (abs(a) + (beta[j - 1] if j > 0 else 0.0)):
             return alpha[:j + 1], beta[:j + 1]
         vm, v = v, w / b
     return alpha, beta
@@ -545,7 +547,16 @@ def ritz_bounds(alpha: np.ndarray, beta: np.ndarray, margin_frac: float = 0.01):
     width = th[-1] - th[0]
     m_lo = max(2.0 * res_lo, margin_frac * width)
     m_hi = max(2.0 * res_hi, margin_frac * width)
-    return th[0] - m_lo, th[-1] + m_hi, th[0], th[-1]
+    e0, e1 = th[0] - m_lo, th[-1] + m_hi
+    # reading for a degenerate spectrum (the paper gives none): the interval is
+    # at least 1e-3 of the Ritz values' magnitude wide (1e-3 around zero),
+    # centred on them, so that there is a scaling (Eq. 2)
+    mag = max(abs(th[0]), abs(th[-1]))
+    wmin = 1e-3 * (mag if mag > 0.0 else 1.0)
+    if e1 - e0 < wmin:
+        c = 0.5 * (th[0] + th[-1])
+        e0, e1 = min(e0, c - 0.5 * wmin), max(e1, c + 0.5 * wmin)
+    return e0, e1, th[0], th[-1]
 
 
 # ----------------------------------------------------------------------------

@@ -35,7 +35,7 @@ EXPORTS = [
     "cheb_masked_product", "cheb_transpose", "cheb_restrict", "cheb_trace_workspace_size", "cheb_trace",
     "cheb_penalty_trace", "cheb_mu_search", "cheb_mu_search_noalloc", "cheb_newton_schulz", "cheb_newton_schulz_isqrt",
     "cheb_plan_col_info", "cheb_penalty_check", "cheb_mu_nodes", "cheb_lagrange_weights", "cheb_bounds_spd",
-    "cheb_series_value", "cheb_bounds_warm", "cheb_plan_set_gather_builder", "cheb_plan_col_lists_copy",
+    "cheb_series_value", "cheb_bounds_warm", "cheb_plan_set_gather_builder", "cheb_plan_lists_copy", "cheb_set_plan_builder",
     "cheb_ssf_export_size", "cheb_ssf_export", "cheb_ssf_import_pattern", "cheb_ssf_import_values",
 ]
 
@@ -103,7 +103,8 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
         "cheb_ssf_export": ([P(CBsr), i64, p, p, p, p], i32),
         "cheb_ssf_import_pattern": ([i64, i64, p, P(i64), p, p, p], i32),
         "cheb_ssf_import_values": ([P(CBsr), i64, p, p, p, i64, p], i32),
-        "cheb_plan_col_lists_copy": ([p, i32, p, ctypes.c_size_t, P(ctypes.c_size_t), p], i32),
+        "cheb_plan_lists_copy": ([p, i32, p, ctypes.c_size_t, P(ctypes.c_size_t), p], i32),
+        "cheb_set_plan_builder": ([i32], i32),
         "cheb_bounds_warm": ([P(CBsr), i32, p, dbl, P(dbl), P(dbl), P(dbl), P(dbl), p, ctypes.c_size_t, p], i32),
         "cheb_lagrange_weights": ([P(dbl), i32, dbl, P(dbl)], i32),
         "cheb_bounds_spd": ([P(CBsr), i32, p, dbl, P(dbl), P(dbl), p, sz, p], i32),
@@ -239,17 +240,18 @@ class Plan:
         self._ws = _ws(nbytes.value, P_out.row_ptr.device)
         _check(lib.cheb_plan_bind(h, ctypes.c_void_p(_aligned(self._ws)), nbytes.value, s))
 
-    def attach_operator(self, L: Bsr, stream=None, gather: str = "device") -> "Plan":
+    def attach_operator(self, L: Bsr, stream=None, gather: str | None = None) -> "Plan":
         """cheb_plan_attach_operator + cheb_plan_bind_operator: row lists for operator pattern L.
 
         gather: "device" (the gather-plan kernels) or "host" (the reference host
-        builder) for the column-order kernel's lists."""
+        builders) for the lists; None keeps the builder the plan was made with."""
         lib = load()
         nbytes = ctypes.c_size_t(0)
         s = _stream(stream)
-        if gather not in ("device", "host"):
-            raise ValueError(f"attach_operator: gather must be 'device' or 'host', not {gather!r}")
-        _check(lib.cheb_plan_set_gather_builder(self.handle, 1 if gather == "host" else 0))
+        if gather is not None:
+            if gather not in ("device", "host"):
+                raise ValueError(f"attach_operator: gather must be 'device' or 'host', not {gather!r}")
+            _check(lib.cheb_plan_set_gather_builder(self.handle, 1 if gather == "host" else 0))
         cb = L.c()
         _check(lib.cheb_plan_attach_operator(self.handle, ctypes.byref(cb), ctypes.byref(nbytes), s))
         self._op_ws = _ws(nbytes.value, L.row_ptr.device)
@@ -393,17 +395,29 @@ def plan_col_info(plan: Plan) -> tuple[int, int, int]:
     return a.value, b.value, c.value
 
 
-def plan_col_lists(plan: Plan, stream=None) -> list[torch.Tensor]:
-    """cheb_plan_col_lists_copy of all six column-kernel lists, as device byte tensors."""
+def plan_lists(plan: Plan, which, stream=None) -> list[torch.Tensor]:
+    """cheb_plan_lists_copy of the tables `which`, as device byte tensors."""
     lib = load()
     out = []
-    for which in range(6):
+    for w in which:
         nb = ctypes.c_size_t(0)
-        _check(lib.cheb_plan_col_lists_copy(plan.handle, which, None, 0, ctypes.byref(nb), _stream(stream)))
+        _check(lib.cheb_plan_lists_copy(plan.handle, w, None, 0, ctypes.byref(nb), _stream(stream)))
         t = torch.empty(max(nb.value, 1), dtype=torch.uint8, device=plan.P_out.row_ptr.device)
-        _check(lib.cheb_plan_col_lists_copy(plan.handle, which, _ptr(t), t.numel(), ctypes.byref(nb), _stream(stream)))
+        _check(lib.cheb_plan_lists_copy(plan.handle, w, _ptr(t), t.numel(), ctypes.byref(nb), _stream(stream)))
         out.append(t[:nb.value])
     return out
+
+
+def plan_col_lists(plan: Plan, stream=None) -> list[torch.Tensor]:
+    """The six column-kernel lists (cheb_plan_lists_copy 0-5)."""
+    return plan_lists(plan, range(6), stream)
+
+
+def set_plan_builder(builder: str):
+    """cheb_set_plan_builder: "device" (the default) or "host" (the reference builders) for later plans."""
+    if builder not in ("device", "host"):
+        raise ValueError(f"set_plan_builder: 'device' or 'host', not {builder!r}")
+    _check(load().cheb_set_plan_builder(1 if builder == "host" else 0))
 
 
 def ssf_export(A: Bsr, stream=None):

@@ -19,6 +19,8 @@
 //   k_gp_scan    offsets of the panels' chunks and rows.
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -56,45 +58,65 @@ __device__ __forceinline__ int gp_block_max(int v, int *sh) {
     return r;
 }
 
-// out[0] = panels, out[1] = largest union, out[2] = 1 if a single column does
-// not fit (no column kernel for this pattern).  stamp: int32[nbr] set to -1.
+// The panel walk shared by every panel set: within each system [sys_col[s],
+// sys_col[s+1]) (one system 0..nbr when sys_col is NULL) the block columns are
+// taken in order, and a panel is closed when P columns are in it or the next
+// column would take its union of rows above ucap or its blocks above bcap.
+// panels: (first column, columns, union rows, 0) per panel; aux (or NULL):
+// (blocks, system) per panel.  out[0] = panels, out[1] = largest union, out[2]
+// = 1 if a single column does not fit, out[3] = most blocks of a panel.
+// stamp: int32[nbr] set to -1.
 __global__ void __launch_bounds__(GP_NT) k_gp_panels(const int64_t *rp, const int32_t *ci, int64_t nbr, int P,
-                                                     int ucap, int32_t *stamp, int32_t *panels, int64_t *out) {
+                                                     int64_t ucap, int64_t bcap, const int64_t *sys_col, int nsys,
+                                                     int32_t *stamp, int32_t *panels, int32_t *aux, int64_t *out) {
     __shared__ int64_t sh[GP_NWARP];
     const int tid = threadIdx.x;
-    int64_t j = 0;
-    int32_t panel = 0, mu = 0;
-    while (j < nbr) {
-        int cnt = 0, ncols = 0;
-        const int64_t j0 = j;
-        while (j < nbr && ncols < P) {
-            int64_t add = 0;
-            for (int64_t e = rp[j] + tid; e < rp[j + 1]; e += GP_NT) add += stamp[ci[e]] != panel;
-            add = gp_block_sum(add, sh);  // reads of column j all happen before this barrier
-            if (cnt + add > ucap) break;
-            for (int64_t e = rp[j] + tid; e < rp[j + 1]; e += GP_NT) stamp[ci[e]] = panel;
-            __syncthreads();
-            cnt += (int)add;
-            ++ncols;
-            ++j;
+    int32_t panel = 0;
+    int64_t mu = 0, mb = 0;
+    for (int sy = 0; sy < nsys; ++sy) {
+        int64_t j = sys_col ? sys_col[sy] : 0;
+        const int64_t end = sys_col ? sys_col[sy + 1] : nbr;
+        while (j < end) {
+            int64_t cnt = 0, nblk = 0;
+            int ncols = 0;
+            const int64_t j0 = j;
+            while (j < end && ncols < P) {
+                const int64_t len = rp[j + 1] - rp[j];
+                int64_t add = 0;
+                for (int64_t e = rp[j] + tid; e < rp[j + 1]; e += GP_NT) add += stamp[ci[e]] != panel;
+                add = gp_block_sum(add, sh);  // reads of column j all happen before this barrier
+                if (cnt + add > ucap || nblk + len > bcap) break;
+                for (int64_t e = rp[j] + tid; e < rp[j + 1]; e += GP_NT) stamp[ci[e]] = panel;
+                __syncthreads();
+                cnt += add;
+                nblk += len;
+                ++ncols;
+                ++j;
+            }
+            if (ncols == 0) {
+                if (tid == 0) out[2] = 1;
+                return;
+            }
+            if (tid == 0) {
+                panels[4 * panel] = (int32_t)j0;
+                panels[4 * panel + 1] = ncols;
+                panels[4 * panel + 2] = (int32_t)cnt;
+                panels[4 * panel + 3] = 0;
+                if (aux) {
+                    aux[2 * panel] = (int32_t)nblk;
+                    aux[2 * panel + 1] = sy;
+                }
+            }
+            mu = max(mu, cnt);
+            mb = max(mb, nblk);
+            ++panel;
         }
-        if (ncols == 0) {
-            if (tid == 0) out[2] = 1;
-            return;
-        }
-        if (tid == 0) {
-            panels[4 * panel] = (int32_t)j0;
-            panels[4 * panel + 1] = ncols;
-            panels[4 * panel + 2] = cnt;
-            panels[4 * panel + 3] = 0;
-        }
-        mu = max(mu, cnt);
-        ++panel;
     }
     if (tid == 0) {
         out[0] = panel;
         out[1] = mu;
         out[2] = 0;
+        out[3] = mb;
     }
 }
 
@@ -370,7 +392,148 @@ __global__ void __launch_bounds__(1024) k_gp_scan(const int64_t *v, int64_t n, i
     }
 }
 
-// Dynamic shared memory of k_gp_rows: bitmap words (+ the fill pass's histogram).
+// ---------------------------------------------------------------------------
+// The plan of P_out itself, on the device: checks, transposition map, the
+// longest block row.
+
+// first[0]: first row whose row_ptr range is decreasing or leaves [0, nnzb];
+// first[1]: first row with a column out of range; first[2]: first row whose
+// columns do not strictly ascend; first[3]: first row without its diagonal
+// block (nbr where none).  *maxlen: the longest row.
+__global__ void k_pc_check(const int64_t *rp, const int32_t *ci, int64_t nbr, int64_t nnzb, int64_t *first,
+                           int32_t *maxlen) {
+    const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (I >= nbr) return;
+    const int64_t a = rp[I], b = rp[I + 1];
+    if (a < 0 || b > nnzb || b < a) {
+        atomicMin(reinterpret_cast<long long *>(first), (long long)I);
+        return;
+    }
+    atomicMax(maxlen, (int32_t)(b - a < (int64_t)INT32_MAX ? b - a : (int64_t)INT32_MAX));
+    bool diag = false;
+    for (int64_t p = a; p < b; ++p) {
+        const int32_t c = ci[p];
+        if (c < 0 || c >= nbr) {
+            atomicMin(reinterpret_cast<long long *>(first + 1), (long long)I);
+            return;
+        }
+        if (p > a && c <= ci[p - 1]) {
+            atomicMin(reinterpret_cast<long long *>(first + 2), (long long)I);
+            return;
+        }
+        diag |= c == I;
+    }
+    if (!diag) atomicMin(reinterpret_cast<long long *>(first + 3), (long long)I);
+}
+
+// tperm[p] = position of block (J, I) for block p = (I, J); *bad = the first
+// block without a transpose (nnzb where none).  Runs on a checked pattern.
+__global__ void k_pc_tperm(const int64_t *rp, const int32_t *ci, int64_t nbr, int64_t nnzb, int32_t *tperm,
+                           int64_t *bad) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= nnzb) return;
+    const int64_t I = row_of(rp, nbr, p);
+    const int64_t q = find_in_row(rp, ci, ci[p], (int32_t)I);
+    if (q < 0)
+        atomicMin(reinterpret_cast<long long *>(bad), (long long)p);
+    else
+        tperm[p] = (int32_t)q;
+}
+
+// Checks of an operator pattern (n blocks): first[0] rows decreasing or out of
+// [0, n] or longer than 65536 blocks; first[1] a column out of range.
+__global__ void k_op_check(const int64_t *rp, const int32_t *ci, int64_t nbr, int64_t n, int64_t *first) {
+    const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (I >= nbr) return;
+    const int64_t a = rp[I], b = rp[I + 1];
+    if (a < 0 || b > n || b < a || b - a > 65536) {
+        atomicMin(reinterpret_cast<long long *>(first), (long long)I);
+        return;
+    }
+    for (int64_t p = a; p < b; ++p)
+        if (ci[p] < 0 || ci[p] >= nbr) {
+            atomicMin(reinterpret_cast<long long *>(first + 1), (long long)I);
+            return;
+        }
+}
+
+// Row lists of one panel set (the FP64 step kernel's and the resident
+// kernel's): per panel (pairs[2p], pairs[2p+1] = first column, columns), per
+// union row in increasing order, the operator row's blocks whose column is in
+// the union as (offset in the operator row << 16 | union slot).  Count pass:
+// cnt[p] entries, nrow[p] = union rows + 1.  Fill pass: row pointers from
+// row_base[p] (global entry offsets from ent_off[p]) and the entries.
+template <bool FILL>
+__global__ void __launch_bounds__(GP_NT) k_rl_rows(const int64_t *rp, const int32_t *ci, int64_t nbr,
+                                                   const int64_t *lrp, const int32_t *lci, const int32_t *pairs,
+                                                   int maxu, int64_t *cnt, int64_t *nrow, const int64_t *ent_off,
+                                                   const int64_t *row_base, int32_t *lrow_ptr, uint32_t *lent,
+                                                   int32_t *err) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x;
+    const int64_t p = blockIdx.x;
+    const int j0 = pairs[2 * p], nc = pairs[2 * p + 1];
+    const int64_t nw = (nbr + 31) / 32;
+    uint2 *bits = reinterpret_cast<uint2 *>(dsm);
+    int *ulist = reinterpret_cast<int *>(dsm + (((size_t)nw * sizeof(uint2) + 15) & ~(size_t)15));
+    for (int64_t w = tid; w < nw; w += GP_NT) bits[w] = make_uint2(0u, 0u);
+    __syncthreads();
+    for (int q = 0; q < nc; ++q)
+        for (int64_t e = rp[j0 + q] + tid; e < rp[j0 + q + 1]; e += GP_NT) {
+            const int K = ci[e];
+            atomicOr(&bits[K >> 5].x, 1u << (K & 31));
+        }
+    __syncthreads();
+    const int64_t chunk = (nw + GP_NT - 1) / GP_NT;
+    const int64_t wb = min(nw, (int64_t)tid * chunk), we = min(nw, wb + chunk);
+    int c = 0;
+    for (int64_t w = wb; w < we; ++w) c += __popc(bits[w].x);
+    int nu;
+    int run = block_excl_scan<GP_NWARP>(c, wsum, &nu);
+    if (nu > maxu) {  // uniform
+        if (tid == 0) atomicExch(err, 1);
+        return;
+    }
+    for (int64_t w = wb; w < we; ++w) {
+        unsigned m = bits[w].x;
+        bits[w].y = (unsigned)run;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            ulist[run++] = (int)(w * 32 + b);
+            m &= m - 1u;
+        }
+    }
+    __syncthreads();
+    // thread t takes union rows [u0, u1) in order; a block scan gives offsets
+    const int rch = (nu + GP_NT - 1) / GP_NT, u0 = min(nu, tid * rch), u1 = min(nu, u0 + rch);
+    int mine = 0;
+    for (int u = u0; u < u1; ++u) {
+        const int I = ulist[u];
+        for (int64_t a = lrp[I]; a < lrp[I + 1]; ++a) mine += rank_of(bits, lci[a]) >= 0;
+    }
+    int total;
+    int off = block_excl_scan<GP_NWARP>(mine, wsum, &total);
+    if (!FILL) {
+        if (tid == 0) {
+            cnt[p] = total;
+            nrow[p] = nu + 1;
+        }
+        return;
+    }
+    const int64_t e0 = ent_off[p], r0 = row_base[p];
+    for (int u = u0; u < u1; ++u) {
+        const int I = ulist[u];
+        lrow_ptr[r0 + u] = (int32_t)(e0 + off);
+        for (int64_t a = lrp[I]; a < lrp[I + 1]; ++a) {
+            const int sl = rank_of(bits, lci[a]);
+            if (sl >= 0) lent[e0 + off++] = ((uint32_t)(a - lrp[I]) << 16) | (uint32_t)sl;
+        }
+    }
+    if (tid == 0) lrow_ptr[r0 + nu] = (int32_t)(e0 + total);
+}
+
+// Dynamic shared memory of k_gp_rows: bitmap words (+ the fill pass's histogram).// Dynamic shared memory of k_gp_rows: bitmap words (+ the fill pass's histogram).
 static size_t gp_dyn_smem(int64_t nbr, bool fill) {
     const size_t bits = align_up((size_t)((nbr + 31) / 32) * sizeof(uint2), 16);
     return bits + (fill ? (GP_HMAX + 1) * sizeof(int) : 0);
@@ -410,7 +573,8 @@ int col_build_device(cheb_plan *plan, const cheb_bsr *L, int32_t ucap, cudaStrea
     int32_t *err = reinterpret_cast<int32_t *>(out + 4);
     CHEB_CUDA(cudaMemsetAsync(stamp, 0xff, nbr * 4, s));
     CHEB_CUDA(cudaMemsetAsync(out, 0, 8 * 8, s));
-    k_gp_panels<<<1, GP_NT, 0, s>>>(plan->rp, plan->ci, nbr, COL_P, ucap, stamp, pan, out);
+    k_gp_panels<<<1, GP_NT, 0, s>>>(plan->rp, plan->ci, nbr, COL_P, ucap, INT64_MAX, nullptr, 1, stamp, pan, nullptr,
+                                    out);
     CHEB_TRY(check_launch("k_gp_panels"));
     int64_t h_out[3];
     CHEB_CUDA(cudaMemcpyAsync(h_out, out, sizeof(h_out), cudaMemcpyDeviceToHost, s));
@@ -488,6 +652,146 @@ int col_build_device(cheb_plan *plan, const cheb_bsr *L, int32_t ucap, cudaStrea
     c.device = true;
     guard.armed = false;
     plan->col = std::move(c);
+    return CHEB_OK;
+}
+
+}  // namespace cheb
+
+namespace cheb {
+
+// ---------------------------------------------------------------------------
+// Host-side launchers of the plan kernels (plan.cu drives them).
+
+int gp_check_pattern(const int64_t *rp, const int32_t *ci, int64_t nbr, int64_t nnzb, int64_t first[4],
+                     int32_t *maxlen, cudaStream_t s) {
+    int64_t *d = nullptr;
+    CHEB_CUDA(cudaMallocAsync(&d, 5 * 8, s));
+    const int64_t init[5] = {nbr, nbr, nbr, nbr, 0};
+    CHEB_CUDA(cudaMemcpyAsync(d, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    k_pc_check<<<(unsigned)((nbr + 255) / 256), 256, 0, s>>>(rp, ci, nbr, nnzb, d,
+                                                           reinterpret_cast<int32_t *>(d + 4));
+    const int rc = check_launch("k_pc_check");
+    int64_t h[5] = {0, 0, 0, 0, 0};
+    if (rc == CHEB_OK) CHEB_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaFreeAsync(d, s));
+    CHEB_CUDA(cudaStreamSynchronize(s));
+    CHEB_TRY(rc);
+    for (int i = 0; i < 4; ++i) first[i] = h[i];
+    int32_t ml;
+    std::memcpy(&ml, &h[4], 4);
+    *maxlen = ml;
+    return CHEB_OK;
+}
+
+int gp_tperm(const int64_t *rp, const int32_t *ci, int64_t nbr, int64_t nnzb, int32_t *tperm, int64_t *bad,
+             cudaStream_t s) {
+    int64_t *d = nullptr;
+    CHEB_CUDA(cudaMallocAsync(&d, 8, s));
+    CHEB_CUDA(cudaMemcpyAsync(d, &nnzb, 8, cudaMemcpyHostToDevice, s));
+    k_pc_tperm<<<(unsigned)((nnzb + 255) / 256), 256, 0, s>>>(rp, ci, nbr, nnzb, tperm, d);
+    const int rc = check_launch("k_pc_tperm");
+    if (rc == CHEB_OK) CHEB_CUDA(cudaMemcpyAsync(bad, d, 8, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaFreeAsync(d, s));
+    CHEB_CUDA(cudaStreamSynchronize(s));
+    return rc;
+}
+
+int gp_walk(const int64_t *rp, const int32_t *ci, int64_t nbr, int P, int64_t ucap, int64_t bcap,
+            const std::vector<int64_t> &sys_col, std::vector<int32_t> &panels4, std::vector<int32_t> &aux,
+            int64_t out[4], cudaStream_t s) {
+    const int nsys = (int)sys_col.size() - 1;
+    size_t off = 0;
+    auto at = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    const size_t o_stamp = at(nbr * 4), o_pan = at(4 * nbr * 4), o_aux = at(2 * nbr * 4), o_out = at(4 * 8),
+                 o_sys = at(sys_col.size() * 8);
+    char *scr = nullptr;
+    CHEB_CUDA(cudaMalloc(&scr, off));
+    struct Free {
+        char *p;
+        ~Free() { cudaFree(p); }
+    } free_scr{scr};
+    int32_t *stamp = reinterpret_cast<int32_t *>(scr + o_stamp), *pan = reinterpret_cast<int32_t *>(scr + o_pan),
+            *ax = reinterpret_cast<int32_t *>(scr + o_aux);
+    int64_t *dout = reinterpret_cast<int64_t *>(scr + o_out), *dsys = reinterpret_cast<int64_t *>(scr + o_sys);
+    CHEB_CUDA(cudaMemsetAsync(stamp, 0xff, nbr * 4, s));
+    CHEB_CUDA(cudaMemsetAsync(dout, 0, 4 * 8, s));
+    CHEB_CUDA(cudaMemcpyAsync(dsys, sys_col.data(), sys_col.size() * 8, cudaMemcpyHostToDevice, s));
+    k_gp_panels<<<1, GP_NT, 0, s>>>(rp, ci, nbr, P, ucap, bcap, dsys, nsys, stamp, pan, ax, dout);
+    CHEB_TRY(check_launch("k_gp_panels"));
+    CHEB_CUDA(cudaMemcpyAsync(out, dout, 4 * 8, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaStreamSynchronize(s));
+    if (out[2]) return CHEB_OK;  // the caller reports the column that does not fit
+    panels4.resize(4 * out[0]);
+    aux.resize(2 * out[0]);
+    CHEB_CUDA(cudaMemcpyAsync(panels4.data(), pan, panels4.size() * 4, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaMemcpyAsync(aux.data(), ax, aux.size() * 4, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaStreamSynchronize(s));
+    return CHEB_OK;
+}
+
+int gp_check_operator(const cheb_bsr *L, int64_t nbr, int64_t first[2], cudaStream_t s) {
+    int64_t *d = nullptr;
+    CHEB_CUDA(cudaMallocAsync(&d, 2 * 8, s));
+    const int64_t init[2] = {nbr, nbr};
+    CHEB_CUDA(cudaMemcpyAsync(d, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    k_op_check<<<(unsigned)((nbr + 255) / 256), 256, 0, s>>>(L->row_ptr, L->col_idx, nbr, L->nnzb, d);
+    const int rc = check_launch("k_op_check");
+    if (rc == CHEB_OK) CHEB_CUDA(cudaMemcpyAsync(first, d, 2 * 8, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaFreeAsync(d, s));
+    CHEB_CUDA(cudaStreamSynchronize(s));
+    return rc;
+}
+
+int row_lists_device(const int64_t *rp, const int32_t *ci, int64_t nbr, const cheb_bsr *L, const int32_t *pairs,
+                     int64_t np, int maxu, RowLists &out, cudaStream_t s) {
+    if (np == 0) return CHEB_OK;
+    const size_t dyn = (((size_t)((nbr + 31) / 32) * sizeof(uint2) + 15) & ~(size_t)15) + (size_t)maxu * 4;
+    if (dyn > (size_t)CHEB_MAX_DYN_SMEM - 2048)
+        return fail(CHEB_ERR_NOSPACE, "cheb_plan_attach_operator: %zu bytes of panel bitmap and union", dyn);
+    CHEB_CUDA(cudaFuncSetAttribute(k_rl_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    CHEB_CUDA(cudaFuncSetAttribute(k_rl_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    int64_t *scr = nullptr;  // cnt, nrow [np]; ent_off, row_base [np + 1]; error flag
+    CHEB_CUDA(cudaMalloc(&scr, (4 * np + 3) * 8));
+    struct Free {
+        int64_t *p;
+        ~Free() { cudaFree(p); }
+    } free_scr{scr};
+    int64_t *cnt = scr, *nrow = scr + np, *ent_off = scr + 2 * np, *row_base = scr + 3 * np + 1;
+    int32_t *err = reinterpret_cast<int32_t *>(scr + 4 * np + 2);
+    CHEB_CUDA(cudaMemsetAsync(err, 0, 4, s));
+    k_rl_rows<false><<<(unsigned)np, GP_NT, dyn, s>>>(rp, ci, nbr, L->row_ptr, L->col_idx, pairs, maxu, cnt, nrow,
+                                                      nullptr, nullptr, nullptr, nullptr, err);
+    k_gp_scan<<<1, 1024, 0, s>>>(cnt, np, ent_off);
+    k_gp_scan<<<1, 1024, 0, s>>>(nrow, np, row_base);
+    CHEB_TRY(check_launch("row lists count", 3));
+    int64_t tot[2];
+    int32_t h_err = 0;
+    CHEB_CUDA(cudaMemcpyAsync(&tot[0], ent_off + np, 8, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaMemcpyAsync(&tot[1], row_base + np, 8, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaStreamSynchronize(s));
+    if (h_err) return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: panel union above the plan's maximum");
+    if (tot[0] >= (int64_t)INT32_MAX)
+        return fail(CHEB_ERR_NOSPACE, "cheb_plan_attach_operator: %lld list entries exceed the int32 offsets",
+                    (long long)tot[0]);
+    out.device = true;
+    out.n_base = np;
+    out.n_ptr = tot[1];
+    out.n_ent = tot[0];
+    CHEB_CUDA(cudaMalloc(&out.tmp, out.bytes()));
+    Carve cv(out.tmp, out.bytes());
+    out.d_base = cv.take<int64_t>(np);
+    out.d_ptr = cv.take<int32_t>(std::max<int64_t>(out.n_ptr, 1));
+    out.d_ent = cv.take<uint32_t>(std::max<int64_t>(out.n_ent, 1));
+    CHEB_CUDA(cudaMemcpyAsync(out.d_base, row_base, np * 8, cudaMemcpyDeviceToDevice, s));
+    k_rl_rows<true><<<(unsigned)np, GP_NT, dyn, s>>>(rp, ci, nbr, L->row_ptr, L->col_idx, pairs, maxu, nullptr,
+                                                     nullptr, ent_off, row_base, out.d_ptr, out.d_ent, err);
+    CHEB_TRY(check_launch("row lists fill"));
+    CHEB_CUDA(cudaStreamSynchronize(s));
     return CHEB_OK;
 }
 

@@ -84,9 +84,13 @@ __global__ void k_lz_finish(LzState *st, int what, int step) {
         if (what == 0) st->out[7] = sqrt(r);
         else if (what == 1) st->alpha[step] = r;
         else {
+            // a beta at rounding level of the step's scale is a breakdown: the
+            // Krylov space is invariant (e.g. a multiple of the identity), and
+            // later steps would only amplify rounding noise
             const double b = sqrt(r);
             st->beta[step] = b;
-            if (b == 0.0) st->kk = step + 1;
+            const double ref = fabs(st->alpha[step]) + (step > 0 ? st->beta[step - 1] : 0.0);
+            if (b == 0.0 || b <= 1e-12 * ref) st->kk = step + 1;
         }
     }
 }
@@ -202,8 +206,18 @@ __global__ void k_tridiag(LzState *st, double margin_frac, double *scratch) {
     const double rlo = fabs(bl * slo), rhi = fabs(bl * shi);
     const double width = th[1] - th[0];
     const double mlo = fmax(2.0 * rlo, margin_frac * width), mhi = fmax(2.0 * rhi, margin_frac * width);
-    st->out[0] = th[0] - mlo;
-    st->out[1] = th[1] + mhi;
+    double e0 = th[0] - mlo, e1 = th[1] + mhi;
+    // a (near-)degenerate spectrum still gets an interval to scale by: at
+    // least 1e-3 of its magnitude (1e-3 around zero), centred on the Ritz values
+    const double mag = fmax(fabs(th[0]), fabs(th[1]));
+    const double wmin = 1e-3 * (mag > 0.0 ? mag : 1.0);
+    if (e1 - e0 < wmin) {
+        const double c = 0.5 * (th[0] + th[1]);
+        e0 = fmin(e0, c - 0.5 * wmin);
+        e1 = fmax(e1, c + 0.5 * wmin);
+    }
+    st->out[0] = e0;
+    st->out[1] = e1;
     st->out[2] = th[0];
     st->out[3] = th[1];
     st->out[4] = rlo;

@@ -44,6 +44,93 @@ extern "C" int cheb_tile_info(int32_t precision, int32_t tile, int32_t *panel_wi
     return CHEB_OK;
 }
 
+// 0: plans and lists built by device kernels (gather.cu); 1: on host threads
+// (the reference builders, bit-identical)
+static int32_t g_plan_host = 0;
+
+extern "C" int cheb_set_plan_builder(int32_t host) {
+    if (host != 0 && host != 1) return fail(CHEB_ERR_INVALID, "cheb_set_plan_builder: 0 (device) or 1 (host)");
+    g_plan_host = host;
+    return CHEB_OK;
+}
+
+static void free_row_lists(RowLists &l) {
+    if (l.tmp) cudaFree(l.tmp);
+    l.tmp = nullptr;
+}
+
+// cheb_plan_create on the device: checks, transposition map and the two panel
+// walks run as kernels on P_out's device arrays; only the panel tables (a few
+// integers per panel) come back to the host.
+static int plan_create_device(cheb_plan *plan, const std::vector<int64_t> &sys_col, const TileCfg &cfg,
+                              int esz, size_t budget, cudaStream_t s) {
+    const int64_t nbr = plan->nbr, nnzb = plan->nnzb;
+    int64_t ends[2];
+    CHEB_CUDA(cudaMemcpyAsync(&ends[0], plan->rp, 8, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaMemcpyAsync(&ends[1], plan->rp + nbr, 8, cudaMemcpyDeviceToHost, s));
+    CHEB_CUDA(cudaStreamSynchronize(s));
+    if (ends[0] != 0 || ends[1] != nnzb) return fail(CHEB_ERR_INVALID, "cheb_plan_create: row_ptr does not span nnzb");
+    int64_t first[4];
+    int32_t maxlen = 1;
+    CHEB_TRY(gp_check_pattern(plan->rp, plan->ci, nbr, nnzb, first, &maxlen, s));
+    if (first[0] < nbr) return fail(CHEB_ERR_INVALID, "row_ptr not monotone at row %lld", (long long)first[0]);
+    if (first[1] < nbr) return fail(CHEB_ERR_INVALID, "col_idx out of range in row %lld", (long long)first[1]);
+    if (first[2] < nbr) return fail(CHEB_ERR_INVALID, "col_idx not strictly ascending in row %lld", (long long)first[2]);
+    if (first[3] < nbr) return fail(CHEB_ERR_INVALID, "diagonal block missing in row %lld", (long long)first[3]);
+    CHEB_CUDA(cudaMalloc(&plan->tmp_tperm, std::max<int64_t>(nnzb, 1) * 4));
+    int64_t bad = nnzb;
+    CHEB_TRY(gp_tperm(plan->rp, plan->ci, nbr, nnzb, plan->tmp_tperm, &bad, s));
+    if (bad < nnzb) return fail(CHEB_ERR_INVALID, "pattern not symmetric: block %lld has no transpose", (long long)bad);
+    maxlen = std::max<int32_t>(maxlen, 1);
+    // step-kernel panels
+    std::vector<int32_t> pan4, aux;
+    int64_t out[4];
+    CHEB_TRY(gp_walk(plan->rp, plan->ci, nbr, plan->P, plan->ucap, INT64_MAX, {0, nbr}, pan4, aux, out, s));
+    if (out[2]) return fail(CHEB_ERR_NOSPACE, "a column does not fit the shared-memory panel of %d rows", plan->ucap);
+    plan->n_panels = out[0];
+    plan->max_union = (int32_t)out[1];
+    plan->h_panels.resize(2 * out[0]);
+    for (int64_t p = 0; p < out[0]; ++p) {
+        plan->h_panels[2 * p] = pan4[4 * p];
+        plan->h_panels[2 * p + 1] = pan4[4 * p + 1];
+    }
+    // resident panels, as in the host builder
+    const int64_t nw = (nbr + 31) / 32;
+    const int P = plan->P;
+    auto bcap_for = [&](int64_t ucap) {
+        int64_t lo = 0, hi = (int64_t)P * maxlen;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) / 2;
+            if (res_layout(nw, ucap, mid, P, esz, cfg.NW).total <= budget) lo = mid; else hi = mid - 1;
+        }
+        return lo;
+    };
+    int64_t Ucap = std::min<int64_t>(2 * (int64_t)maxlen, 32767);
+    int64_t Bcap = bcap_for(Ucap);
+    while (Bcap < maxlen && Ucap > maxlen) {
+        Ucap = std::max<int64_t>(maxlen, Ucap * 3 / 4);
+        Bcap = bcap_for(Ucap);
+    }
+    if (Bcap < maxlen) return fail(CHEB_ERR_NOSPACE, "a column of %d blocks does not fit a resident panel", maxlen);
+    CHEB_TRY(gp_walk(plan->rp, plan->ci, nbr, P, Ucap, Bcap, sys_col, pan4, aux, out, s));
+    if (out[2]) return fail(CHEB_ERR_NOSPACE, "a column does not fit a resident panel");
+    const int64_t nr = out[0];
+    plan->h_rpanels.resize(2 * nr);
+    plan->h_rpanel_sys.resize(nr);
+    for (int64_t p = 0; p < nr; ++p) {
+        plan->h_rpanels[2 * p] = pan4[4 * p];
+        plan->h_rpanels[2 * p + 1] = pan4[4 * p + 1];
+        plan->h_rpanel_sys[p] = aux[2 * p + 1];
+    }
+    const int nsys = (int)sys_col.size() - 1;
+    plan->h_sys_rpanel.assign(nsys + 1, (int32_t)nr);
+    for (int64_t p = nr - 1; p >= 0; --p) plan->h_sys_rpanel[plan->h_rpanel_sys[p]] = (int32_t)p;
+    plan->n_rpanels = nr;
+    plan->max_union_res = (int32_t)out[1];
+    plan->max_nblk_res = (int32_t)out[3];
+    return CHEB_OK;
+}
+
 static int plan_create_impl(const cheb_bsr *P_out, int32_t precision, int32_t tile, int32_t nsys,
                             const int64_t *sys_row_start, cheb_plan **out, size_t *plan_ws_bytes, void *stream) {
     if (!out || !plan_ws_bytes) return fail(CHEB_ERR_INVALID, "cheb_plan_create: NULL output");
@@ -69,9 +156,43 @@ static int plan_create_impl(const cheb_bsr *P_out, int32_t precision, int32_t ti
         sys_col[0] = 0;
         sys_col[1] = nbr;
     }
+    cudaStream_t s = as_stream(stream);
+    auto plan_ws = [](const cheb_plan *pl) {
+        return align_up(pl->nnzb * 4) + align_up(pl->h_panels.size() * 4) + align_up(64) +
+               align_up(pl->h_rpanels.size() * 4) + align_up(pl->h_rpanel_sys.size() * 4) +
+               align_up(pl->h_sys_rpanel.size() * 4);
+    };
+    if (!g_plan_host) {
+        auto plan = new cheb_plan();
+        plan->nbr = nbr;
+        plan->nnzb = nnzb;
+        plan->rp = P_out->row_ptr;
+        plan->ci = P_out->col_idx;
+        plan->precision = precision;
+        plan->nsys = nsys;
+        plan->h_sys_col = sys_col;
+        plan->gather_host = 0;
+        const TileCfg cfg = tile_cfg(precision, tile);
+        const int esz = (precision == CHEB_F64 || precision == CHEB_F64X) ? 8 : 4;
+        plan->tile = tile;
+        plan->P = cfg.P;
+        plan->NW = cfg.NW;
+        plan->minb = cfg.MINB;
+        const size_t budget = smem_budget(cfg.MINB);
+        plan->ucap = union_capacity(nbr, cfg.P, esz, cfg.NW, budget);
+        const int rc = plan_create_device(plan, sys_col, cfg, esz, budget, s);
+        if (rc != CHEB_OK) {
+            if (plan->tmp_tperm) cudaFree(plan->tmp_tperm);
+            delete plan;
+            return rc;
+        }
+        plan->ws_bytes = plan_ws(plan);
+        *plan_ws_bytes = plan->ws_bytes;
+        *out = plan;
+        return CHEB_OK;
+    }
     std::vector<int64_t> rp(nbr + 1);
     std::vector<int32_t> ci(nnzb);
-    cudaStream_t s = as_stream(stream);
     CHEB_CUDA(cudaMemcpyAsync(rp.data(), P_out->row_ptr, (nbr + 1) * 8, cudaMemcpyDeviceToHost, s));
     CHEB_CUDA(cudaMemcpyAsync(ci.data(), P_out->col_idx, nnzb * 4, cudaMemcpyDeviceToHost, s));
     CHEB_CUDA(cudaStreamSynchronize(s));
@@ -94,6 +215,7 @@ static int plan_create_impl(const cheb_bsr *P_out, int32_t precision, int32_t ti
     plan->precision = precision;
     plan->nsys = nsys;
     plan->h_sys_col = sys_col;
+    plan->gather_host = 1;
     plan->h_tperm.resize(nnzb);
     for (int64_t I = 0; I < nbr; ++I) {
         for (int64_t p = rp[I]; p < rp[I + 1]; ++p) {
@@ -205,9 +327,7 @@ static int plan_create_impl(const cheb_bsr *P_out, int32_t precision, int32_t ti
         plan->max_union_res = max_union;
         plan->max_nblk_res = max_nblk;
     }
-    plan->ws_bytes = align_up(nnzb * 4) + align_up(plan->h_panels.size() * 4) + align_up(64) +
-                     align_up(plan->h_rpanels.size() * 4) + align_up(plan->h_rpanel_sys.size() * 4) +
-                     align_up(plan->h_sys_rpanel.size() * 4);
+    plan->ws_bytes = plan_ws(plan);
     *plan_ws_bytes = plan->ws_bytes;
     *out = plan;
     return CHEB_OK;
@@ -238,7 +358,10 @@ extern "C" int cheb_plan_bind(cheb_plan *plan, void *ws, size_t ws_bytes, void *
     plan->d_rpanel_sys = cv.take<int32_t>(plan->h_rpanel_sys.size());
     plan->d_sys_rpanel = cv.take<int32_t>(plan->h_sys_rpanel.size());
     cudaStream_t s = as_stream(stream);
-    CHEB_CUDA(cudaMemcpyAsync(plan->d_tperm, plan->h_tperm.data(), plan->nnzb * 4, cudaMemcpyHostToDevice, s));
+    if (plan->tmp_tperm)
+        CHEB_CUDA(cudaMemcpyAsync(plan->d_tperm, plan->tmp_tperm, plan->nnzb * 4, cudaMemcpyDeviceToDevice, s));
+    else
+        CHEB_CUDA(cudaMemcpyAsync(plan->d_tperm, plan->h_tperm.data(), plan->nnzb * 4, cudaMemcpyHostToDevice, s));
     CHEB_CUDA(cudaMemcpyAsync(plan->d_panels, plan->h_panels.data(), plan->h_panels.size() * 4,
                               cudaMemcpyHostToDevice, s));
     CHEB_CUDA(cudaMemsetAsync(plan->d_counter, 0, 64, s));
@@ -250,6 +373,10 @@ extern "C" int cheb_plan_bind(cheb_plan *plan, void *ws, size_t ws_bytes, void *
                               cudaMemcpyHostToDevice, s));
     // The host vectors are read by the async copies: finish them before returning.
     CHEB_CUDA(cudaStreamSynchronize(s));
+    if (plan->tmp_tperm) {
+        cudaFree(plan->tmp_tperm);
+        plan->tmp_tperm = nullptr;
+    }
     plan->bound = true;
     return CHEB_OK;
 }
@@ -283,7 +410,12 @@ extern "C" int cheb_plan_col_info(const cheb_plan *plan, int64_t *n_panels, int3
 }
 
 extern "C" int cheb_plan_destroy(cheb_plan *plan) {
-    if (plan) col_free(plan->col);
+    if (plan) {
+        col_free(plan->col);
+        free_row_lists(plan->lists);
+        free_row_lists(plan->rlists);
+        if (plan->tmp_tperm) cudaFree(plan->tmp_tperm);
+    }
     delete plan;
     return CHEB_OK;
 }
@@ -294,19 +426,28 @@ extern "C" int cheb_plan_set_gather_builder(cheb_plan *plan, int32_t host) {
     return CHEB_OK;
 }
 
-extern "C" int cheb_plan_col_lists_copy(const cheb_plan *plan, int32_t which, void *dst, size_t dst_bytes,
-                                        size_t *bytes, void *stream) {
-    if (!plan || !bytes || which < 0 || which > 5)
-        return fail(CHEB_ERR_INVALID, "cheb_plan_col_lists_copy: bad arguments");
+extern "C" int cheb_plan_lists_copy(const cheb_plan *plan, int32_t which, void *dst, size_t dst_bytes,
+                                    size_t *bytes, void *stream) {
+    if (!plan || !bytes || which < 0 || which > 16) return fail(CHEB_ERR_INVALID, "cheb_plan_lists_copy: bad arguments");
+    if (!plan->bound) return fail(CHEB_ERR_INVALID, "cheb_plan_lists_copy: plan not bound");
     const ColLists &c = plan->col;
-    if (!c.built || !c.bound) return fail(CHEB_ERR_INVALID, "cheb_plan_col_lists_copy: no bound column-kernel lists");
+    if (which <= 5 && !(c.built && c.bound))
+        return fail(CHEB_ERR_INVALID, "cheb_plan_lists_copy: no bound column-kernel lists");
+    if (which >= 11 && !plan->op_bound) return fail(CHEB_ERR_INVALID, "cheb_plan_lists_copy: no bound row lists");
     const int64_t np = c.n_panels;
-    const void *src[6] = {c.d_panels, c.d_wchunk, c.d_wrow, c.d_rows, c.d_ent, c.d_slot};
-    const size_t n[6] = {(size_t)np * 16, (size_t)np * (c.NW + 1) * 4, (size_t)np * (c.NW + 1) * 4,
-                         (size_t)c.n_rows * 4, (size_t)c.n_entries * 4, (size_t)c.n_slot * 2};
+    const RowLists &a = plan->lists, &b = plan->rlists;
+    const void *src[17] = {c.d_panels, c.d_wchunk, c.d_wrow, c.d_rows, c.d_ent, c.d_slot,
+                           plan->d_tperm, plan->d_panels, plan->d_rpanels, plan->d_rpanel_sys, plan->d_sys_rpanel,
+                           a.d_base, a.d_ptr, a.d_ent, b.d_base, b.d_ptr, b.d_ent};
+    const size_t n[17] = {(size_t)np * 16, (size_t)np * (c.NW + 1) * 4, (size_t)np * (c.NW + 1) * 4,
+                          (size_t)c.n_rows * 4, (size_t)c.n_entries * 4, (size_t)c.n_slot * 2,
+                          (size_t)plan->nnzb * 4, plan->h_panels.size() * 4, plan->h_rpanels.size() * 4,
+                          plan->h_rpanel_sys.size() * 4, plan->h_sys_rpanel.size() * 4,
+                          (size_t)a.n_base * 8, (size_t)a.n_ptr * 4, (size_t)a.n_ent * 4,
+                          (size_t)b.n_base * 8, (size_t)b.n_ptr * 4, (size_t)b.n_ent * 4};
     *bytes = n[which];
     if (!dst) return CHEB_OK;
-    if (dst_bytes < n[which]) return fail(CHEB_ERR_NOSPACE, "cheb_plan_col_lists_copy: %zu < %zu bytes", dst_bytes, n[which]);
+    if (dst_bytes < n[which]) return fail(CHEB_ERR_NOSPACE, "cheb_plan_lists_copy: %zu < %zu bytes", dst_bytes, n[which]);
     cudaStream_t s = as_stream(stream);
     if (n[which]) CHEB_CUDA(cudaMemcpyAsync(dst, src[which], n[which], cudaMemcpyDeviceToDevice, s));
     return CHEB_OK;
@@ -387,6 +528,9 @@ static int make_row_lists(int64_t nbr, const std::vector<int32_t> &panels, int64
     out.h_base.swap(lrow_base);
     out.h_ptr.swap(lrow_ptr);
     out.h_ent.swap(lent);
+    out.n_base = (int64_t)out.h_base.size();
+    out.n_ptr = (int64_t)out.h_ptr.size();
+    out.n_ent = (int64_t)out.h_ent.size();
     return CHEB_OK;
 }
 
@@ -396,9 +540,54 @@ extern "C" int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, siz
     if (plan->ucap > 65535) return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: union too large");
     const int64_t nbr = plan->nbr, nnzL = L->nnzb;
     if (nnzL >= (int64_t)INT32_MAX) return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: operator too large");
+    cudaStream_t s = as_stream(stream);
+    free_row_lists(plan->lists);
+    free_row_lists(plan->rlists);
+    col_free(plan->col);
+    plan->lists = RowLists();
+    plan->rlists = RowLists();
+    plan->col = ColLists();
+    plan->op_ws_bytes = 0;
+    plan->op_bound = false;
+    if (!plan->gather_host) {
+        // every list built by device kernels from the device patterns (gather.cu)
+        if (!plan->bound) return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: bind the plan first");
+        int64_t ends[2];
+        CHEB_CUDA(cudaMemcpyAsync(&ends[0], L->row_ptr, 8, cudaMemcpyDeviceToHost, s));
+        CHEB_CUDA(cudaMemcpyAsync(&ends[1], L->row_ptr + nbr, 8, cudaMemcpyDeviceToHost, s));
+        CHEB_CUDA(cudaStreamSynchronize(s));
+        if (ends[0] != 0 || ends[1] != nnzL) return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: bad row_ptr");
+        int64_t first[2];
+        CHEB_TRY(gp_check_operator(L, nbr, first, s));
+        if (first[0] < nbr)
+            return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: row_ptr decreasing or row longer than 65536 blocks at row %lld",
+                        (long long)first[0]);
+        if (first[1] < nbr)
+            return fail(CHEB_ERR_INVALID, "cheb_plan_attach_operator: column out of range in row %lld", (long long)first[1]);
+        RowLists lists, rlists;
+        int rc = row_lists_device(plan->rp, plan->ci, nbr, L, plan->d_panels, plan->n_panels, plan->max_union, lists, s);
+        if (rc == CHEB_OK && plan->n_rpanels > 0)
+            rc = row_lists_device(plan->rp, plan->ci, nbr, L, plan->d_rpanels, plan->n_rpanels, plan->max_union_res,
+                                  rlists, s);
+        if (rc != CHEB_OK) {
+            free_row_lists(lists);
+            free_row_lists(rlists);
+            return rc;
+        }
+        plan->op_rp = L->row_ptr;
+        plan->op_ci = L->col_idx;
+        plan->lists = std::move(lists);
+        plan->rlists = std::move(rlists);
+        if (plan->precision == CHEB_F32 || plan->precision == CHEB_BF16) {
+            rc = col_build_device(plan, L, col_ucap(), s);
+            if (rc != CHEB_OK && rc != CHEB_ERR_NOSPACE) return rc;
+        }
+        plan->op_ws_bytes = plan->lists.bytes() + plan->rlists.bytes() + plan->col.bytes();
+        *op_ws_bytes = plan->op_ws_bytes;
+        return CHEB_OK;
+    }
     std::vector<int64_t> rp(nbr + 1), lrp(nbr + 1);
     std::vector<int32_t> ci(plan->nnzb), lci(nnzL);
-    cudaStream_t s = as_stream(stream);
     CHEB_CUDA(cudaMemcpyAsync(rp.data(), plan->rp, (nbr + 1) * 8, cudaMemcpyDeviceToHost, s));
     CHEB_CUDA(cudaMemcpyAsync(ci.data(), plan->ci, plan->nnzb * 4, cudaMemcpyDeviceToHost, s));
     CHEB_CUDA(cudaMemcpyAsync(lrp.data(), L->row_ptr, (nbr + 1) * 8, cudaMemcpyDeviceToHost, s));
@@ -424,12 +613,8 @@ extern "C" int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, siz
     // reduced-precision plans: the column-order step kernel's lists (left
     // unbuilt when a panel column or an operator row does not fit it; the
     // per-step products then use the ranking kernel)
-    col_free(plan->col);
-    plan->col = ColLists();
     if (plan->precision == CHEB_F32 || plan->precision == CHEB_BF16) {
-        // the gather-plan kernels (gather.cu) by default; the host threads of
-        // colstep.cu when asked (the same lists, bit for bit)
-        const int rc = plan->gather_host ? col_build(plan, rp, ci, lrp, lci) : col_build_device(plan, L, col_ucap(), s);
+        const int rc = col_build(plan, rp, ci, lrp, lci);
         if (rc != CHEB_OK && rc != CHEB_ERR_NOSPACE) return rc;
     }
     plan->op_ws_bytes = plan->lists.bytes() + plan->rlists.bytes() + plan->col.bytes();
@@ -440,7 +625,17 @@ extern "C" int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, siz
 
 // Device copies of one panel set's lists, carved from the operator workspace.
 static int bind_row_lists(RowLists &l, Carve &cv, cudaStream_t s) {
-    if (l.h_base.empty()) return CHEB_OK;
+    if (l.n_base == 0) return CHEB_OK;
+    if (l.device) {
+        char *dst = cv.take<char>(l.bytes());
+        if (!cv.fits()) return fail(CHEB_ERR_NOSPACE, "cheb_plan_bind_operator: workspace too small");
+        CHEB_CUDA(cudaMemcpyAsync(dst, l.tmp, l.bytes(), cudaMemcpyDeviceToDevice, s));
+        const ptrdiff_t d = dst - static_cast<char *>(l.tmp);
+        l.d_base = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(l.d_base) + d);
+        l.d_ptr = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(l.d_ptr) + d);
+        l.d_ent = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(l.d_ent) + d);
+        return CHEB_OK;
+    }
     l.d_base = cv.take<int64_t>(l.h_base.size());
     l.d_ptr = cv.take<int32_t>(l.h_ptr.size());
     l.d_ent = cv.take<uint32_t>(std::max<size_t>(l.h_ent.size(), 1));
@@ -464,6 +659,8 @@ extern "C" int cheb_plan_bind_operator(cheb_plan *plan, void *ws, size_t ws_byte
     CHEB_TRY(col_bind(plan->col, cv, s));
     CHEB_CUDA(cudaStreamSynchronize(s));
     col_release_host(plan->col);
+    free_row_lists(plan->lists);
+    free_row_lists(plan->rlists);
     // the device copies are the only ones needed from here on
     for (RowLists *l : {&plan->lists, &plan->rlists}) {
         std::vector<int32_t>().swap(l->h_ptr);

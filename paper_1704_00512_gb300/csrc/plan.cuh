@@ -14,13 +14,17 @@ struct RowLists {
     std::vector<int64_t> h_base;  // [panels] first row pointer of each panel
     std::vector<int32_t> h_ptr;   // [sum of (union + 1) over panels] entry offsets
     std::vector<uint32_t> h_ent;  // entries
+    int64_t n_base = 0, n_ptr = 0, n_ent = 0;  // sizes of the three arrays
     int64_t *d_base = nullptr;
     int32_t *d_ptr = nullptr;
     uint32_t *d_ent = nullptr;
+    // built by the device kernels: the d_ arrays live in tmp until bound
+    bool device = false;
+    void *tmp = nullptr;
     size_t bytes() const {
-        return h_base.empty() ? 0
-                              : ::cheb::align_up(h_base.size() * 8) + ::cheb::align_up(h_ptr.size() * 4) +
-                                    ::cheb::align_up(std::max<size_t>(h_ent.size(), 1) * 4);
+        return n_base == 0 ? 0
+                           : ::cheb::align_up((size_t)n_base * 8) + ::cheb::align_up((size_t)std::max<int64_t>(n_ptr, 1) * 4) +
+                                 ::cheb::align_up((size_t)std::max<int64_t>(n_ent, 1) * 4);
     }
 };
 
@@ -78,6 +82,7 @@ struct cheb_plan {
     int32_t max_union = 0;  // largest union of row lists over a panel
     int32_t ucap = 0;       // union rows that fit in shared memory
     std::vector<int32_t> h_tperm;   // slot of (J,I) for each slot (I,J)
+    int32_t *tmp_tperm = nullptr;   // the same, built on the device, until cheb_plan_bind
     std::vector<int32_t> h_panels;  // pairs (first column, column count)
     // panels of the resident kernel (whole expansion per thread block); they
     // never straddle two systems of a block-diagonal batch
@@ -252,6 +257,17 @@ int col_build(cheb_plan *plan, const std::vector<int64_t> &rp, const std::vector
 // the same lists built by device kernels from the device patterns (gather.cu)
 int col_build_device(cheb_plan *plan, const cheb_bsr *L, int32_t ucap, cudaStream_t s);
 void col_free(ColLists &c);
+// the plan of P_out and the row lists on the device (gather.cu)
+int gp_check_pattern(const int64_t *rp, const int32_t *ci, int64_t nbr, int64_t nnzb, int64_t first[4],
+                     int32_t *maxlen, cudaStream_t s);
+int gp_tperm(const int64_t *rp, const int32_t *ci, int64_t nbr, int64_t nnzb, int32_t *tperm, int64_t *bad,
+             cudaStream_t s);
+int gp_walk(const int64_t *rp, const int32_t *ci, int64_t nbr, int P, int64_t ucap, int64_t bcap,
+            const std::vector<int64_t> &sys_col, std::vector<int32_t> &panels4, std::vector<int32_t> &aux,
+            int64_t out[4], cudaStream_t s);
+int gp_check_operator(const cheb_bsr *L, int64_t nbr, int64_t first[2], cudaStream_t s);
+int row_lists_device(const int64_t *rp, const int32_t *ci, int64_t nbr, const cheb_bsr *L, const int32_t *pairs,
+                     int64_t np, int maxu, RowLists &out, cudaStream_t s);
 int col_bind(ColLists &c, Carve &cv, cudaStream_t s);
 void col_release_host(ColLists &c);
 bool col_usable(const cheb_plan *plan, const cheb_bsr *Mt);

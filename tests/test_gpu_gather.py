@@ -82,3 +82,47 @@ def test_expansion_through_the_device_gather_plan():
     for j in range(nf):
         a, b = acc[j].cpu().numpy(), ex.acc[j].vals
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5
+
+
+def _plan(dP, prec, dL, builder, sys_starts=None):
+    cg.set_plan_builder(builder)
+    try:
+        if sys_starts is None:
+            plan = cg.Plan(dP, prec)
+        else:
+            plan = cg.BatchedPlan(dP, sys_starts, precision=prec)
+        return plan.attach_operator(dL)
+    finally:
+        cg.set_plan_builder("device")
+
+
+@pytest.mark.parametrize("prec", [cg.F64, cg.F32, cg.F64X])
+@pytest.mark.parametrize("n_atoms,r_c,r_buf,seed", [(33, 3.0, 1.5, 1), (300, 6.0, 3.0, 2), (1000, 8.0, 4.0, 3)])
+def test_device_plan_bit_identical_to_host(prec, n_atoms, r_c, r_buf, seed):
+    # cheb_plan_create + attach with no host copy of the patterns: checks,
+    # transposition map, step and resident panels, both row-list sets and the
+    # column kernel's lists, against the host builders
+    s = synth.make_system(n_atoms, r_c, seed)
+    S, H, P_out = pipelines.system_mats(s, r_buf)
+    dP = dbsr(P_out.row_ptr, P_out.col_idx)
+    dL = dbsr(H.row_ptr, H.col_idx, H.vals)
+    dev = _plan(dP, prec, dL, "device")
+    host = _plan(dP, prec, dL, "host")
+    assert dev.info() == host.info() and cg.plan_resident_info(dev) == cg.plan_resident_info(host)
+    which = list(range(6, 17)) + (list(range(6)) if prec == cg.F32 else [])
+    for w, a, b in zip(which, cg.plan_lists(dev, which), cg.plan_lists(host, which)):
+        assert a.numel() == b.numel() and torch.equal(a, b), w
+
+
+def test_device_batched_plan_bit_identical_to_host():
+    systems = [synth.make_system(n, 4.0, 20 + i) for i, n in enumerate((40, 90, 25, 60))]
+    Ps = [pipelines.system_mats(x, 2.0) for x in systems]
+    bd = cg.block_diag([dbsr(P.row_ptr, P.col_idx, np.zeros((P.nnzb, 4, 4))) for _, _, P in Ps])
+    Hd = cg.block_diag([dbsr(H.row_ptr, H.col_idx, H.vals) for _, H, _ in Ps])
+    starts = np.concatenate([[0], np.cumsum([x.n_atoms for x in systems])]).tolist()
+    dP = cg.Bsr(bd.row_ptr, bd.col_idx)
+    dev = _plan(dP, cg.F64, Hd, "device", starts)
+    host = _plan(dP, cg.F64, Hd, "host", starts)
+    which = list(range(6, 17))
+    for w, a, b in zip(which, cg.plan_lists(dev, which), cg.plan_lists(host, which)):
+        assert a.numel() == b.numel() and torch.equal(a, b), w

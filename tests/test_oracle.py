@@ -642,3 +642,25 @@ def test_penalty_side_shows_in_the_sign_pattern_of_the_moments():
         ex = ref.chebyshev_expand(ref.scale(S, emin, emax), P_out, np.zeros((1, n)))
         assert abs(ref.penalty_trace(ex.t, -40.0, emin, emax)) >= 1.0
         assert (-1 if ex.t[-1] * ex.t[-2] < 0 else 1) == side
+
+
+def test_lanczos_bounds_of_a_multiple_of_the_identity():
+    # a degenerate spectrum: Lanczos breaks down after one step (the Krylov
+    # space of c I is invariant), theta = c exactly, and the interval is widened
+    # to 1e-3 |c| around c, so that it still contains the spectrum
+    n = 6
+    rp = np.arange(n + 1, dtype=np.int64)
+    ci = np.arange(n, dtype=np.int32)
+    for c in (1.0, -2.5, 0.0):
+        A = ref.Bsr(rp, ci, np.stack([c * np.eye(4)] * n))
+        alpha, beta = ref.lanczos(A, np.ones(4 * n), 40)
+        assert len(alpha) == 1 and alpha[0] == pytest.approx(c, abs=1e-15)
+        e0, e1, t0, t1 = ref.ritz_bounds(alpha, beta, 0.01)
+        w = 1e-3 * (abs(c) if c != 0.0 else 1.0)
+        assert e0 < c < e1 and e1 - e0 == pytest.approx(w, rel=1e-12)
+    # a spectrum of normal width is untouched by the floor
+    Ad = np.diag(np.linspace(-1.0, 2.0, 4 * n))
+    A = ref.Bsr(rp, ci, np.stack([Ad[4 * i:4 * i + 4, 4 * i:4 * i + 4] for i in range(n)]))
+    alpha, beta = ref.lanczos(A, np.ones(4 * n), 40)
+    e0, e1, t0, t1 = ref.ritz_bounds(alpha, beta, 0.01)
+    assert e0 <= -1.0 and e1 >= 2.0 and e1 - e0 < 3.2
