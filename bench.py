@@ -733,12 +733,12 @@ def solve_step_equivalents(n_terms: int, n_pass1: int, nnz_out: int, nnz_H: int)
     return (n_pass1 - 2) + (n_terms - 2) + 4 * nnz_out / nnz_H
 
 
-def cpu_baseline(sysm, cfg, n_terms, n_pass1, earlier_rounds=()) -> dict:
-    """earlier_rounds: term counts of two-pass solves that preceded the accepted
+def cpu_baseline(sysm, cfg, n_terms, n_pass1, earlier_solves=()) -> dict:
+    """earlier_solves: term counts of two-pass solves that preceded the accepted
     one (the smearing loop), each counted as a whole solve."""
     t_step, nnz_out = oracle_sample(sysm, cfg, 1)
     eq = solve_step_equivalents(n_terms, n_pass1, nnz_out, sysm.nnzb)
-    eq += sum(solve_step_equivalents(n, n, nnz_out, sysm.nnzb) for n in earlier_rounds)
+    eq += sum(solve_step_equivalents(n, n, nnz_out, sysm.nnzb) for n in earlier_solves)
     return {"value": 1.0 / (t_step * eq), "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
             "extrapolated": True,
             "sample": f"1 FP64 oracle recursion step of the same system timed ({t_step:.2f}s), extrapolated by "

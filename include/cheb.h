@@ -118,11 +118,13 @@ int cheb_pattern_build(const double *xyz, int64_t n_atoms, double box_L, double 
  * The step kernel comes in several tile shapes per precision (panel width,
  * warps per block, blocks per SM); cheb_tile_count / cheb_tile_info list them.
  *
- * cheb_plan_create (host-returning): reads P_out's row_ptr/col_idx (device)
- * to the host, checks symmetry, sortedness and diagonal blocks
- * (CHEB_ERR_INVALID otherwise), groups columns into panels for tile shape
- * `tile` (-1 = the default shape of the precision), and returns a
- * host-allocated plan and the device workspace it needs in *plan_ws_bytes.
+ * cheb_plan_create (host-returning): checks P_out (device row_ptr/col_idx:
+ * symmetry, sortedness, diagonal blocks; CHEB_ERR_INVALID otherwise), builds
+ * its transposition map and groups columns into panels for tile shape `tile`
+ * (-1 = the default shape of the precision) -- with device kernels unless
+ * cheb_set_plan_builder(1) asked for the host builders, see below -- and
+ * returns a host-allocated plan and the device workspace it needs in
+ * *plan_ws_bytes.
  * cheb_plan_bind copies the plan tables into caller device memory plan_ws
  * (>= plan_ws_bytes, 256-byte aligned); the plan then refers to that memory,
  * which must stay valid until cheb_plan_destroy.  P_out's row_ptr/col_idx
@@ -157,7 +159,10 @@ int cheb_plan_info(const cheb_plan *plan, int64_t *n_panels, int32_t *panel_widt
  * row_ptr/col_idx pointers reads its entries from the lists instead of
  * ranking the operator's rows at every step; other operators use the ranking
  * path.  Both paths multiply the same blocks in the same order, so results
- * are bit-identical.  Attaching again replaces the lists. */
+ * are bit-identical.  Attaching again replaces the lists.  The lists are
+ * built by device kernels from the device arrays of P_out and L (the plan
+ * must be bound first) unless the host builders were chosen (see "Builders"
+ * below). */
 int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, size_t *op_ws_bytes, void *stream);
 
 /* Column-order step kernel of reduced-precision plans.  For a CHEB_F32 or
@@ -225,7 +230,11 @@ int cheb_scale(const cheb_bsr *M, double emin, double emax, double *out, void *s
 /* ---------------------------------------------------------------------------
  * Spectral bounds (Sec. "Determination of the eigenvalue bounds ..."): k steps
  * of plain Lanczos on the FP64 matrix M from start vector v0 (device
- * double[4*nbr]; NULL means the all-ones vector), then the extreme eigenvalues
+ * double[4*nbr]; NULL means the default v_i = 1 + u_i/2, u_i = (top 53 bits
+ * of splitmix64(i)) / 2^53, i = 0..4 nbr - 1: positive, with a component along
+ * every eigenvector of structured matrices), stopping early at a breakdown
+ * (beta_j <= 1e-12 (|alpha_j| + beta_{j-1}): an invariant Krylov space), then
+ * the extreme eigenvalues
  * theta_min/max of the Lanczos tridiagonal and the residuals
  * beta_k |s| of their Ritz pairs.  *emin = theta_min - m_lo, *emax = theta_max
  * + m_hi with m = max(2*residual, margin_frac*(theta_max - theta_min)).

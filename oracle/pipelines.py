@@ -23,8 +23,12 @@ def system_mats(sysm, r_buf: float):
 
 
 def lanczos_start(n_rows: int) -> np.ndarray:
-    """The all-ones start vector (the C ABI's default)."""
-    return np.ones(n_rows)
+    """The C ABI's default start vector: v_i = 1 + u_i / 2 with u_i the top 53
+    bits of SplitMix64(i) over 2^53 (a positive vector with a component along
+    every eigenvector; the all-ones vector can lie in a small invariant subspace)."""
+    from .mlp import splitmix64
+    u = (splitmix64(np.arange(n_rows, dtype=np.uint64)) >> np.uint64(11)).astype(np.float64) / 9007199254740992.0
+    return 1.0 + 0.5 * u
 
 
 def powers(S: ref.Bsr, P_out: ref.Bsr, exponents, bounds, n_terms: int, newton_schulz: bool = False):

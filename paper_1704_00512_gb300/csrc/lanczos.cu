@@ -116,6 +116,22 @@ __global__ void k_fill(double *x, int64_t n, double val) {
         x[i] = val;
 }
 
+// The default start vector: x_i = 1 + u_i / 2, u_i = (splitmix64(i) >> 11) / 2^53
+// (SplitMix64: Steele, Lea and Flood, 2014).  Positive like the all-ones
+// vector, but with a component along every eigenvector of a structured matrix
+// (the all-ones vector can lie in a small invariant subspace, e.g. of the
+// overlap of one atom's basis functions, and Lanczos would then stop inside it).
+__device__ __forceinline__ uint64_t lz_splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__global__ void k_fill_start(double *x, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = 1.0 + 0.5 * ((double)(lz_splitmix64((uint64_t)i) >> 11) * (1.0 / 9007199254740992.0));
+}
+
 // Number of eigenvalues of the tridiagonal (a, b) below x (Sturm sequence).
 __device__ int sturm_count(const double *a, const double *b, int k, double x) {
     int c = 0;
@@ -253,8 +269,8 @@ extern "C" int cheb_bounds(const cheb_bsr *M, int32_t k, const double *v0, doubl
     // start vector (copied so v0 stays untouched) and its normalisation
     if (v0) CHEB_CUDA(cudaMemcpyAsync(w, v0, n * 8, cudaMemcpyDeviceToDevice, s));
     else {
-        k_fill<<<LZ_GRID, LZ_NT, 0, s>>>(w, n, 1.0);
-        CHEB_TRY(check_launch("k_fill"));
+        k_fill_start<<<LZ_GRID, LZ_NT, 0, s>>>(w, n);
+        CHEB_TRY(check_launch("k_fill_start"));
     }
     k_lz_vec<<<LZ_GRID, LZ_NT, 0, s>>>(0, n, w, v, vm, st, 0);
     k_lz_finish<<<1, LZ_NT, 0, s>>>(st, 0, 0);

@@ -43,7 +43,7 @@ def relF_cols(got_full, want_cols, P_out, cols):
 def case(n_atoms, r_c, r_buf, seed):
     s = synth.make_system(n_atoms, r_c, seed)
     S, H, P_out = pipelines.system_mats(s, r_buf)
-    alpha, beta = ref.lanczos(H, np.ones(4 * H.nbr), 40)
+    alpha, beta = ref.lanczos(H, pipelines.lanczos_start(4 * H.nbr), 40)
     lo, hi, _, _ = ref.ritz_bounds(alpha, beta, 0.01)
     return s, H, P_out, lo, hi
 

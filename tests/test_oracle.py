@@ -664,3 +664,20 @@ def test_lanczos_bounds_of_a_multiple_of_the_identity():
     alpha, beta = ref.lanczos(A, np.ones(4 * n), 40)
     e0, e1, t0, t1 = ref.ritz_bounds(alpha, beta, 0.01)
     assert e0 <= -1.0 and e1 >= 2.0 and e1 - e0 < 3.2
+
+
+def test_lanczos_start_vector_sees_every_eigenvalue_of_one_atoms_overlap():
+    # the overlap of one atom's four Gaussians: the all-ones vector lies in a
+    # two-dimensional invariant subspace (Lanczos stops there and misses the
+    # smallest eigenvalue); the default start vector does not
+    s = synth.make_system(1, 1.0, 4)
+    S = ref.Bsr(s.row_ptr, s.col_idx, s.S)
+    w = np.linalg.eigvalsh(S.dense())
+    a1, b1 = ref.lanczos(S, np.ones(4), 40)
+    assert len(a1) == 2 and ref.ritz_bounds(a1, b1)[0] > w[0]
+    a2, b2 = ref.lanczos(S, pipelines.lanczos_start(4), 40)
+    e0, e1, t0, t1 = ref.ritz_bounds(a2, b2)
+    assert len(a2) == 4 and e0 <= w[0] and e1 >= w[-1]
+    assert abs(t0 - w[0]) < 1e-12 and abs(t1 - w[-1]) < 1e-12
+    v = pipelines.lanczos_start(1000)
+    assert v.min() >= 1.0 and v.max() < 1.5 and abs(v.mean() - 1.25) < 0.02
