@@ -705,20 +705,26 @@ def oracle_threads() -> int:
         return os.cpu_count() or 1
 
 
-def col_traffic_per_launch(form: str, n_mu: int, launches_pass, nnz_out: int):
+def col_kernel_measured(text: str | None = None) -> bool:
+    """Whether the column kernel's source (colstep.cu before its host section)
+    is the one COL_TRAFFIC was measured on."""
+    import hashlib
+    if text is None:
+        with open(os.path.join(ROOT, "paper_1704_00512_gb300", "csrc", "colstep.cu"), encoding="utf-8") as f:
+            text = f.read()
+    if COL_KERNEL_END not in text:
+        return False
+    kernel = text[:text.index(COL_KERNEL_END)]
+    return hashlib.sha256(kernel.encode()).hexdigest() == COL_TRAFFIC["colstep_sha256"]
+
+
+def col_traffic_per_launch(form: str, n_mu: int, launches_pass, nnz_out: int, measured: bool | None = None):
     """Measured DRAM bytes per k_colstep launch of a 4-mu solve, scaled to this
     system's P_out blocks and averaged over the solve's two passes; None for
     other forms or when the kernel source differs from the measured one."""
-    import hashlib
     if form != "mu4" or n_mu != 4 or len(launches_pass) != 2:
         return None
-    src = os.path.join(ROOT, "paper_1704_00512_gb300", "csrc", "colstep.cu")
-    with open(src, encoding="utf-8") as f:
-        text = f.read()
-    if COL_KERNEL_END not in text:
-        return None
-    kernel = text[:text.index(COL_KERNEL_END)]
-    if hashlib.sha256(kernel.encode()).hexdigest() != COL_TRAFFIC["colstep_sha256"]:
+    if not (col_kernel_measured() if measured is None else measured):
         return None
     scale = nnz_out / COL_TRAFFIC["blocks_P_out"]
     per = [COL_TRAFFIC["pass1_bytes"], COL_TRAFFIC["pass2_4acc_bytes"]]

@@ -199,7 +199,10 @@ int cheb_plan_attach_operator(cheb_plan *plan, const cheb_bsr *L, size_t *op_ws_
  * transposition map, the panel walks, the operator row lists of both panel
  * sets and the column kernel's lists); only the panel tables -- a few integers
  * per panel -- and sizes come back to the host, and cheb_plan_attach_operator
- * then needs a bound plan.  cheb_set_plan_builder(1) makes later plans use the
+ * then needs a bound plan.  The device builders take scratch device memory
+ * with cudaMalloc during the call (and hold the built tables in it until
+ * cheb_plan_bind / cheb_plan_bind_operator copy them into the caller's
+ * workspace); they are setup calls, not for stream capture.  cheb_set_plan_builder(1) makes later plans use the
  * host threads instead (a copy of the patterns on the host: the reference
  * builders, bit-identical), cheb_set_plan_builder(0) restores the device;
  * cheb_plan_set_gather_builder(plan, host) picks the builder of one plan's

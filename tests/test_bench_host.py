@@ -76,7 +76,10 @@ def test_shipped_proposal_weights_match_the_network():
 
 
 def test_traffic_scales_with_blocks_and_is_tied_to_the_measured_source():
-    t = bench.col_traffic_per_launch("mu4", 4, [100, 200], bench.COL_TRAFFIC["blocks_P_out"] * 2)
+    t = bench.col_traffic_per_launch("mu4", 4, [100, 200], bench.COL_TRAFFIC["blocks_P_out"] * 2, measured=True)
     want = 2 * (bench.COL_TRAFFIC["pass1_bytes"] * 100 + bench.COL_TRAFFIC["pass2_4acc_bytes"] * 200) / 300
     assert t == int(want)
-    assert bench.col_traffic_per_launch("twopass", 1, [100, 100], 10) is None
+    assert bench.col_traffic_per_launch("twopass", 1, [100, 100], 10, measured=True) is None
+    assert bench.col_traffic_per_launch("mu4", 4, [100, 200], 10, measured=False) is None
+    # any change to the kernel text before the host section drops the figure
+    assert not bench.col_kernel_measured("__global__ void k() {}\n" + bench.COL_KERNEL_END)
