@@ -131,3 +131,20 @@ def test_batched_penalty_flags_the_system_whose_bound_is_shrunk():
     # the warm start with the Lanczos bounds themselves solves as before
     again = batched.foe_batched(bp, KT, N_e, tol=1e-9, tol_S=1e-10, use_graphs=False, bounds_H=out["bounds_H"])
     assert relF(again["F"].cpu().numpy(), out["F"].cpu().numpy()) < 1e-12
+
+
+def test_batched_foe_in_the_double_float_mode():
+    # CHEB_F64X through the batched resident kernel (per-system term counts):
+    # the FP64 bar against the oracle, the same bisection decisions
+    systems = _systems()
+    N_e = [2.0 * s.n_atoms for s in systems]
+    bp = batched.BatchedProblem(systems, R_BUF, DEV, precision=cg.F64X)
+    tolN = [1e-9 * n for n in N_e]
+    out = batched.foe_batched(bp, KT, N_e, tol=1e-9, tol_S=1e-10, tol_N=tolN, use_graphs=False)
+    F = out["F"].cpu().numpy()
+    for i, s in enumerate(systems):
+        S, H, P_out = pipelines.system_mats(s, R_BUF)
+        orc = pipelines.foe(S, H, P_out, KT, N_e[i], out["bounds_S"][i], out["n_S"][i], out["bounds_H"][i],
+                            out["n_terms"][i], tol_N=tolN[i])
+        assert relF(F[bp.ooff[i]:bp.ooff[i + 1]], orc["F"].vals) < 1e-10
+        assert out["mu_result"][i]["bits"] == orc["mu"].bits
