@@ -131,3 +131,44 @@ def test_output_pattern_equal_to_operator_pattern():
                         tol_N=1e-9 * N_e)
     assert out["mu_result"]["bits"] == orc["mu"].bits
     assert relF(out["F"].cpu().numpy(), orc["F"].vals) < 1e-10
+
+
+def test_columns_beyond_the_column_kernel_capacity():
+    # a dense 700-row block pattern: every column has 700 rows, more than a
+    # column-kernel panel holds (about 670), so the column kernel's lists are
+    # not built and the per-step products run on the ranking kernel; a tile
+    # whose shared memory cannot hold one column is refused with NOSPACE
+    nb = 700
+    rng = np.random.default_rng(11)
+    rp = np.arange(nb + 1, dtype=np.int64) * nb
+    ci = np.tile(np.arange(nb, dtype=np.int32), nb)
+    B = rng.normal(size=(4 * nb, 4 * nb))
+    Md = (B + B.T) / (4.0 * np.sqrt(4 * nb))  # spectrum inside [-1, 1]
+    vals = Md.reshape(nb, 4, nb, 4).transpose(0, 2, 1, 3).reshape(nb * nb, 4, 4)
+    Mt = ref.Bsr(rp, ci, vals)
+    assert np.max(np.abs(np.linalg.eigvalsh(Md))) < 1.0
+    n = 8
+    c = np.random.default_rng(12).normal(size=(1, n))
+    cols = [0, 351, 699]
+    want = ref.column_expand(Mt, Mt, cols, c)
+    dP = cg.Bsr(torch.as_tensor(rp, device=DEV), torch.as_tensor(ci, device=DEV))
+    dM = cg.Bsr(torch.as_tensor(rp, device=DEV), torch.as_tensor(ci, device=DEV), torch.as_tensor(vals, device=DEV))
+    for prec, tol in ((cg.F32, 1e-5), (cg.F64, 1e-12)):
+        built = 0
+        for tile in range(len(cg.tile_shapes(prec))):
+            try:
+                plan = cg.Plan(dP, prec, tile)
+            except cg.ChebError as e:
+                assert e.code == 7 and "does not fit" in str(e)  # CHEB_ERR_NOSPACE
+                continue
+            plan.attach_operator(dM)
+            assert cg.plan_col_info(plan)[0] == 0  # no column-kernel lists for these columns
+            acc = [torch.zeros((nb * nb, 4, 4), dtype=torch.float64, device=DEV)]
+            cg.expand(plan, dM, n, torch.as_tensor(c, device=DEV), acc, precision=prec, stepwise=True)
+            got = ref.column_blocks(acc[0].cpu().numpy(), Mt, cols)
+            num = sum(np.linalg.norm(a - b) ** 2 for a, b in zip(got, want[0]))
+            den = sum(np.linalg.norm(b) ** 2 for b in want[0])
+            assert np.sqrt(num / den) < tol, (prec, tile)
+            built += 1
+        # a 1-column FP32 tile holds these columns; FP64 tiles may all refuse
+        assert built >= 1 or prec == cg.F64, prec
