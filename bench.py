@@ -283,6 +283,8 @@ def run_cheb(args, rank: int, world: int, local: int):
     torch.cuda.synchronize()
     ts = time.time()
     pb = solve.problem_from_system(sysm, cfg["r_buf"], dev, prec)
+    torch.cuda.synchronize()
+    plans_s = time.time() - ts
     ov = solve.overlap_setup(pb, cfg["tol_S"])
     torch.cuda.synchronize()
     setup_s = time.time() - ts
@@ -441,7 +443,8 @@ def run_cheb(args, rank: int, world: int, local: int):
                    "accumulators": "double-float pairs (FP32 pipe), returned as FP64" if prec == cg.F32 else "fp64",
                    "per_step_input": "H_k = H + 1e-4 k S (new Hamiltonian each step)",
                    "setup_outside_timed_region": "patterns, plans, gather plans, S^-1/2, G (fixed overlap)",
-                   "setup_s": round(setup_s, 2), "parallelism": f"replicas x{world}",
+                   "setup_s": round(setup_s, 2), "patterns_and_plans_s": round(plans_s, 2),
+                   "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (no flush)"},
         "pass_ms": [round(x, 1) for x in p_ms],
         "roofline": roof,
