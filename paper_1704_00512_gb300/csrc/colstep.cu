@@ -299,27 +299,27 @@ __global__ void __launch_bounds__(NW * 32, 1) k_colstep(const ColArgs a) {
     const int nch = (int)(c1 - c0);
     if (nch > 0) {
         constexpr int WC = 32 / CW;  // chunks per window
-        static_assert(WC >= 1 && D - 1 + WC - 1 < 3 * WC, "the producer reads at most two windows ahead");
+        // Chunk n is always in win0 and chunk n + D - 1, whose operator blocks
+        // are issued while chunk n is multiplied, always in win1, both at
+        // window offset jo = n - n0 (n0: first chunk of win0), so that a
+        // word's source lane is jo * CW + e * KG + kg with no window select.
+        static_assert(D - 1 == WC, "the producer runs exactly one window ahead");
         const uint32_t *ew = a.ent + c0 * CW;  // words of the warp's chunks
         const int nw = nch * CW;
         uint32_t win0 = lane < nw ? ld_stream_u32(ew + lane, pstream) : 0u;
         uint32_t win1 = 32 + lane < nw ? ld_stream_u32(ew + 32 + lane, pstream) : 0u;
         uint32_t win2 = 64 + lane < nw ? ld_stream_u32(ew + 64 + lane, pstream) : 0u;
         uint32_t win3 = 96 + lane < nw ? ld_stream_u32(ew + 96 + lane, pstream) : 0u;
-        // word e of K-group kg in chunk c, n0 <= c < n0 + 3 WC (n0: first chunk of win0)
-        auto word_of = [&](int c, int n0, int e) {
-            const int j = c - n0;
-            const uint32_t v = j < WC ? win0 : (j < 2 * WC ? win1 : win2);
-            return __shfl_sync(0xffffffffu, v, (j % WC) * CW + e * KG + kg);
-        };
-        // the lane's part of stage st: 16-byte chunk c of block (e, kg) at
-        // chunk c ^ skw, so that the K-groups' blocks spread over all banks
-        auto produce = [&](int c, int n0) {
+        // the lane's part of stage st for the chunk whose words are in window
+        // value win at source lanes lb + e * KG: 16-byte chunk c of block
+        // (e, kg) at chunk c ^ skw, so that the K-groups' blocks spread over
+        // all banks
+        auto produce = [&](uint32_t win, int lb, int st, bool live) {
             uint32_t words[EK];
 #pragma unroll
-            for (int e = 0; e < EK; ++e) words[e] = word_of(c, n0, e);
-            if (c < nch) {
-                float *dst = stg + (c % D) * CW * 16;
+            for (int e = 0; e < EK; ++e) words[e] = __shfl_sync(0xffffffffu, win, lb + e * KG);
+            if (live) {
+                float *dst = stg + st * CW * 16;
 #pragma unroll
                 for (int e = 0; e < EK; ++e) {
                     const float *src = a.Lv + (int64_t)(words[e] >> COL_SLOT_BITS) * BB;
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_colstep(const ColArgs a) {
             cp_async_commit();
         };
 #pragma unroll
-        for (int i = 0; i < D - 1; ++i) produce(i, 0);
+        for (int i = 0; i < D - 1; ++i) produce(win0, i * CW + kg, i, i < nch);
         // Rows: union slot s, chunks left cl.  A row with blocks in at most two
         // of the panel's columns ("half" row) runs with each column on two
         // lane quads: lane (q, kg) takes column cols[q & 1] and only entry
@@ -374,19 +374,23 @@ __global__ void __launch_bounds__(NW * 32, 1) k_colstep(const ColArgs a) {
         float acc[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) acc[i] = 0.f;
-        // acc += L_IK X[K][col] for staged block b of stage st and slot tc
-        auto multiply = [&](const float *hs, int tc) {
+        // acc += L_IK X[K][col] for staged block b of stage st and slot tc.
+        // Row m of slot tc's block sits at row m ^ (tc & 1): even rows at
+        // m * 4P + d, odd rows at m * 4P - d, d = (tc & 1) * 4P.
+        static_assert(RQ == 2, "slot swizzle of one bit");
+        const float *xcol = X + 4 * col;  // follows col from row to row
+        auto multiply = [&](const float *hs, uint32_t tc) {
             float hc[16];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float4 v = *reinterpret_cast<const float4 *>(hs + 4 * (c ^ skw));
                 hc[4 * c] = v.x; hc[4 * c + 1] = v.y; hc[4 * c + 2] = v.z; hc[4 * c + 3] = v.w;
             }
-            const float *xs = X + (size_t)tc * 16 * P + 4 * col;
-            const int sw = tc & (RQ - 1);
+            const int d = (int)(tc & 1u) * 4 * P;
+            const float *xe = xcol + tc * (16 * P) + d, *xo = xcol + tc * (16 * P) - d;
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
-                const float4 x = *reinterpret_cast<const float4 *>(xs + (m ^ sw) * 4 * P);
+                const float4 x = *reinterpret_cast<const float4 *>((m & 1 ? xo : xe) + m * 4 * P);
 #pragma unroll
                 for (int rr = 0; rr < 4; ++rr) {
                     acc[4 * rr + 0] = fmaf(hc[4 * rr + m], x.x, acc[4 * rr + 0]);
@@ -396,26 +400,31 @@ __global__ void __launch_bounds__(NW * 32, 1) k_colstep(const ColArgs a) {
                 }
             }
         };
-        int n0 = 0, sc = 0;  // first chunk of win0; stage of chunk n
+        // n0: first chunk of win0; lb = (n - n0) * CW + kg; sc, ps: stages of
+        // chunks n and n + D - 1
+        int n0 = 0, lb = kg, sc = 0, ps = D - 1;
         for (int n = 0; n < nch; ++n) {
-            produce(n + D - 1, n0);
+            produce(win1, lb, ps, n + D - 1 < nch);
             cp_async_wait<D - 1>();
             __syncwarp();
             const float *st = stg + sc * CW * 16 + kg * 16;
             if (!half) {
 #pragma unroll
-                for (int e = 0; e < EK; ++e) multiply(st + e * KG * 16, (int)(word_of(n, n0, e) & SM));
+                for (int e = 0; e < EK; ++e)
+                    multiply(st + e * KG * 16, __shfl_sync(0xffffffffu, win0, lb + e * KG) & SM);
             } else {
                 const int e = q >> 1;
-                const int j = n - n0;
-                const uint32_t wv = __shfl_sync(0xffffffffu, j < WC ? win0 : win1, (j % WC) * CW + e * KG + kg);
-                multiply(st + e * KG * 16, (int)(wv & SM));
+                const uint32_t wv = __shfl_sync(0xffffffffu, win0, lb + e * KG);
+                multiply(st + e * KG * 16, wv & SM);
             }
             __syncwarp();
             sc = sc + 1 == D ? 0 : sc + 1;
+            ps = ps + 1 == D ? 0 : ps + 1;
+            lb += CW;
             if (n + 1 - n0 == WC) {
                 // the next window: shift, and fetch the one three windows ahead
                 n0 += WC;
+                lb = kg;
                 win0 = win1;
                 win1 = win2;
                 win2 = win3;
@@ -425,7 +434,18 @@ __global__ void __launch_bounds__(NW * 32, 1) k_colstep(const ColArgs a) {
             if (--cl == 0) {
                 // 3. the row is done: combine the K-groups (a half row's two
                 // lane quads per column first), reduce-scatter, then finish
-                // the lane's elements of block (row s, column col)
+                // the lane's elements of block (row s, column col).  The
+                // accumulators NFP, NFP + 1 (not prefetched at the row's start)
+                // are loaded first, so that the reduce-scatter's shuffles
+                // cover part of their latency.
+                constexpr int NL = NFP > 0 ? 1 : 0;
+                float lv[NL > 0 ? NL : 1][2 * EPL];
+                if (NL > 0 && a.grp && pos >= 0) {
+#pragma unroll
+                    for (int f = 0; f < NL; ++f)
+                        if (NFP + f < a.nf)
+                            ldh_pairs<EPL>(lv[f], a.accp[NFP + f] + ((int64_t)pos * BB + i0) * 2, pstream);
+                }
                 if (half) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], P / 2);
@@ -471,6 +491,9 @@ __global__ void __launch_bounds__(NW * 32, 1) k_colstep(const ColArgs a) {
                                 if (f < NFP) {
 #pragma unroll
                                     for (int j = 0; j < 2 * EPL; ++j) v[j] = av[f < NFP ? f : 0][j];
+                                } else if (f < NFP + NL) {
+#pragma unroll
+                                    for (int j = 0; j < 2 * EPL; ++j) v[j] = lv[f < NFP + NL ? f - NFP : 0][j];
                                 } else {
                                     ldh_pairs<EPL>(v, pa, pstream);
                                 }
@@ -510,6 +533,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_colstep(const ColArgs a) {
                     cl = (int)(rw >> COL_ROW_SHIFT);
                     half = (rw >> COL_SLOT_BITS) & 1u;
                     col = coln;
+                    xcol = X + 4 * col;
                     pos = posn;
                     if (r + 1 < r1) row_col(rwn, coln, posn);
                     else posn = -1;
