@@ -431,9 +431,20 @@ int cheb_series_value(const double *coeffs, const double *moments, int32_t n_ter
  * does not tell, because the penalty polynomial grows outside the interval
  * too; 2 when the trace or those moments are not finite (the recursion
  * overflowed; no side named).  The threshold and alpha are the caller's (the
- * paper leaves both open).  Workspace: 8*n_terms + 8 bytes. */
+ * paper leaves both open); |alpha| is capped at 0.4*n_terms, so that the
+ * penalty polynomial of n_terms terms resolves the exponential's decay.
+ * Workspace: 8*n_terms + 8 bytes. */
 int cheb_penalty_check(const double *moments, int32_t n_terms, double alpha, double threshold,
                        double *value, int32_t *verdict, void *ws, size_t ws_bytes, void *stream);
+
+/* The bound a penalty verdict names, moved out (Eq. 5 and the penalty passage
+ * of Sec. "Determination of the eigenvalue bounds and polynomial degree": the
+ * failing bound has to be adjusted).  bounds: host double[2] (emin < emax),
+ * updated in place: verdict -1 lowers emin, +1 raises emax, 2 (non-finite
+ * trace, side unknown) does both, by frac * (emax - emin); 0 leaves them.
+ * Host only, synchronous; CHEB_ERR_INVALID for a bad verdict, frac < 0 or an
+ * empty interval. */
+int cheb_widen_bounds(double *bounds, int32_t verdict, double frac);
 
 /* ---------------------------------------------------------------------------
  * mu search (Sec. "Fermi Operator Expansion": adjust mu until Tr(KS) = N, by
@@ -561,6 +572,16 @@ int cheb_mlp_adam(float *theta, const float *grad, float *m, float *v, int32_t t
                   void *stream);
 int cheb_mlp_features(const double *moments, int64_t n_rows, double emin, double emax, double N_e,
                       float *features, void *stream);
+
+/* The bracket one network output proposes, in Ha: out (host float[2], a copy
+ * of one row of cheb_mlp_forward's output) holds the scaled mu guess and the
+ * log half-width; with the scaling of Eq. 2 on [emin, emax] (sigma = 2/(emax -
+ * emin), tau = (emin + emax)/2): *mu_hat = out[0]/sigma + tau, *half =
+ * exp(out[1])/sigma clamped to [min_half_kT*kT, max_half_kT*kT].  Host only,
+ * synchronous; CHEB_ERR_INVALID for an empty interval, kT <= 0 or
+ * min_half_kT > max_half_kT. */
+int cheb_mlp_bracket(const float *out, double emin, double emax, double kT, double min_half_kT,
+                     double max_half_kT, double *mu_hat, double *half);
 
 /* ---------------------------------------------------------------------------
  * Segment Storage Format (Sec. "Storage format of the sparse matrices"), for

@@ -35,6 +35,7 @@ EXPORTS = [
     "cheb_masked_product", "cheb_transpose", "cheb_restrict", "cheb_trace_workspace_size", "cheb_trace",
     "cheb_penalty_trace", "cheb_mu_search", "cheb_mu_search_noalloc", "cheb_newton_schulz", "cheb_newton_schulz_isqrt",
     "cheb_plan_col_info", "cheb_penalty_check", "cheb_mu_nodes", "cheb_lagrange_weights", "cheb_bounds_spd",
+    "cheb_widen_bounds", "cheb_mlp_bracket",
     "cheb_series_value", "cheb_bounds_warm", "cheb_plan_set_gather_builder", "cheb_plan_lists_copy", "cheb_set_plan_builder",
     "cheb_ssf_export_size", "cheb_ssf_export", "cheb_ssf_import_pattern", "cheb_ssf_import_values",
 ]
@@ -97,6 +98,8 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
         "cheb_plan_col_info": ([p, P(i64), P(i32), P(i64)], i32),
         "cheb_penalty_check": ([p, i32, dbl, dbl, P(dbl), P(i32), p, sz, p], i32),
         "cheb_mu_nodes": ([dbl, dbl, i32, P(dbl)], i32),
+        "cheb_widen_bounds": ([P(dbl), i32, dbl], i32),
+        "cheb_mlp_bracket": ([P(ctypes.c_float), dbl, dbl, dbl, dbl, dbl, P(dbl), P(dbl)], i32),
         "cheb_series_value": ([p, p, i32, p, p], i32),
         "cheb_plan_set_gather_builder": ([p, i32], i32),
         "cheb_ssf_export_size": ([P(CBsr), P(i64), P(i64), p], i32),
@@ -564,6 +567,22 @@ def mu_nodes(center: float, half: float, n: int) -> list[float]:
     out = (ctypes.c_double * n)()
     _check(load().cheb_mu_nodes(center, half, n, out))
     return list(out)
+
+
+def widen_bounds(bounds, verdict: int, frac: float) -> tuple[float, float]:
+    """cheb_widen_bounds: the bounds with the side a penalty verdict names moved out."""
+    b = (ctypes.c_double * 2)(float(bounds[0]), float(bounds[1]))
+    _check(load().cheb_widen_bounds(b, int(verdict), float(frac)))
+    return b[0], b[1]
+
+
+def mlp_bracket(out, emin: float, emax: float, kT: float, min_half_kT: float, max_half_kT: float):
+    """cheb_mlp_bracket: (mu_hat, half) in Ha from one network output (2 floats)."""
+    o = (ctypes.c_float * 2)(float(out[0]), float(out[1]))
+    mu, half = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().cheb_mlp_bracket(o, emin, emax, kT, min_half_kT, max_half_kT, ctypes.byref(mu),
+                                   ctypes.byref(half)))
+    return mu.value, half.value
 
 
 def lagrange_weights(nodes, x: float) -> list[float]:

@@ -415,6 +415,10 @@ extern "C" int cheb_penalty_check(const double *moments, int32_t n_terms, double
         return fail(CHEB_ERR_INVALID, "cheb_penalty_check: bad arguments");
     if (!ws || ws_bytes < (size_t)n_terms * 8 + 8) return fail(CHEB_ERR_NOSPACE, "cheb_penalty_check: workspace");
     double *out = static_cast<double *>(ws) + n_terms;
+    // |alpha| at most 2/5 of the terms, so that the penalty polynomial of
+    // n_terms terms resolves the exponential's decay length
+    const double amax = 0.4 * n_terms;
+    if (fabs(alpha) > amax) alpha = alpha < 0 ? -amax : amax;
     CHEB_TRY(cheb_penalty_trace(moments, n_terms, alpha, out, ws, (size_t)n_terms * 8, stream));
     double v = 0.0, last[2] = {0.0, 0.0};
     cudaStream_t s = as_stream(stream);
@@ -431,6 +435,28 @@ extern "C" int cheb_penalty_check(const double *moments, int32_t n_terms, double
     if (!finite) *verdict = 2;
     else if (fabs(v) < threshold) *verdict = 0;
     else *verdict = last[0] * last[1] < 0.0 ? -1 : 1;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_widen_bounds(double *bounds, int32_t verdict, double frac) {
+    if (!bounds || !(frac >= 0) || verdict < -1 || verdict > 2 || !(bounds[1] > bounds[0]))
+        return fail(CHEB_ERR_INVALID, "cheb_widen_bounds: bad arguments");
+    const double w = frac * (bounds[1] - bounds[0]);
+    if (verdict == -1 || verdict == 2) bounds[0] -= w;
+    if (verdict == 1 || verdict == 2) bounds[1] += w;
+    return CHEB_OK;
+}
+
+extern "C" int cheb_mlp_bracket(const float *out, double emin, double emax, double kT, double min_half_kT,
+                                double max_half_kT, double *mu_hat, double *half) {
+    if (!out || !mu_hat || !half || !(emax > emin) || !(kT > 0) || !(min_half_kT >= 0) ||
+        !(max_half_kT >= min_half_kT))
+        return fail(CHEB_ERR_INVALID, "cheb_mlp_bracket: bad arguments");
+    // the network works in the scaled variable of Eq. 2: x~ = sigma (e - tau)
+    const double sigma = 2.0 / (emax - emin), tau = 0.5 * (emin + emax);
+    *mu_hat = (double)out[0] / sigma + tau;
+    const double h = exp((double)out[1]) / sigma;
+    *half = fmin(fmax(h, min_half_kT * kT), max_half_kT * kT);
     return CHEB_OK;
 }
 

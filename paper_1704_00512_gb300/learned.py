@@ -17,7 +17,6 @@ Every numerical step runs in libcheb.so; this module sequences calls.
 from __future__ import annotations
 
 import dataclasses
-import math
 import os
 
 import numpy as np
@@ -178,14 +177,12 @@ def foe_learned(pb: solve.Problem, prop: Proposal, kT: float, N_e: float, tol: f
     prepared = prepare(pb) if prepared is None else prepared
     A, Hpt, (e0, e1), G = prepared[:4]
     Hp = prepared[4] if len(prepared) > 4 else None
-    sigma, tau = 2.0 / (e1 - e0), 0.5 * (e0 + e1)
+    tau = 0.5 * (e0 + e1)  # the degree is chosen at the interval centre
     if bracket is None:
         t32 = moments32(pb, Hpt, stepwise=stepwise)
         X = features(pb, t32, (e0, e1), N_e).view(1, N_IN)
         o = prop.forward(X).cpu().numpy()[0]
-        mu_hat = float(o[0]) / sigma + tau
-        half = math.exp(float(o[1])) / sigma
-        half = min(max(half, min_half_kT * kT), max_half_kT * kT)
+        mu_hat, half = L.mlp_bracket(o, e0, e1, kT, min_half_kT, max_half_kT)
     else:
         mu_hat, half = bracket
     mus = L.mu_nodes(mu_hat, half, n_mu)

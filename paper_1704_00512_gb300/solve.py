@@ -184,21 +184,14 @@ def penalty(t: torch.Tensor, m: int, alpha: float = -200.0, threshold: float = 1
     """Eq. 5 on the first min(m, terms) traces t_k = Tr T_k of an expansion:
     (verdict, value), verdict 0 when the spectrum lies in the bounds, -1 / +1
     for the lower / upper bound, 2 for a non-finite trace.  |alpha| (scaled
-    variable) is capped at 2/5 of the terms, so that the penalty polynomial
-    resolves it."""
-    npen = min(m, terms)
-    return L.penalty_check(t, npen, -min(abs(alpha), 0.4 * npen), threshold)
+    variable) is capped by the library at 2/5 of the terms, so that the penalty
+    polynomial resolves it."""
+    return L.penalty_check(t, min(m, terms), alpha, threshold)
 
 
 def widen(bounds: tuple[float, float], verdict: int, frac: float) -> tuple[float, float]:
     """The bound the penalty verdict names, moved out by frac of the interval width."""
-    e0, e1 = bounds
-    w = frac * (e1 - e0)
-    if verdict in (-1, 2):
-        e0 -= w
-    if verdict in (1, 2):
-        e1 += w
-    return e0, e1
+    return L.widen_bounds(bounds, verdict, frac)
 
 
 def foe(pb: Problem, kT: float, N_e: float, tol: float = 1e-10, kind: int = L.FERMI, n_max: int = 16384,
