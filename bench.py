@@ -43,15 +43,15 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # column-order step kernel, from one ncu capture of every k_colstep launch of a
 # 4-mu solve on 3,000 atoms (12,000 rows, r_c 10, r_out 14 bohr: 1,183,812
-# P_out blocks; pass 1 moments only, pass 2 four accumulators; grouped steps
-# included), GB300.  Per-launch traffic scales with the P_out blocks (the
+# P_out blocks; kT 0.05 Ha, 960 terms: 478 pass-1 launches with moments only,
+# 958 pass-2 launches with four accumulators; grouped steps included), GB300.  Per-launch traffic scales with the P_out blocks (the
 # operator has the same share of them).  Valid only for the kernel source it was
 # measured on: the sha256 of colstep.cu's text before its host-builder section
 # (the kernels and their launch code); after any change there the bench reports
 # traffic null.
 COL_KERNEL_END = "// Host: the column kernel's panels and work streams"
-COL_TRAFFIC = {"colstep_sha256": "cc9d95ecc1b85669fcea8afd64036312d5f218382ae48e929d2b0e3a7ef74bb3",
-               "blocks_P_out": 1183812, "pass1_bytes": 463.3e6, "pass2_4acc_bytes": 866.2e6}
+COL_TRAFFIC = {"colstep_sha256": "154741e02d152208e90026c68cebafde56a0824781690b584981970ab666ee15",
+               "blocks_P_out": 1183812, "pass1_bytes": 465.4e6, "pass2_4acc_bytes": 867.9e6}
 SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 
 WORKLOADS = {
