@@ -44,21 +44,24 @@ FALLBACK_HBM_GBS = 6800.0
 # column-order step kernel, from one ncu capture of every k_colstep launch of a
 # 4-mu solve on 3,000 atoms (12,000 rows, r_c 10, r_out 14 bohr: 1,183,812
 # P_out blocks; kT 0.05 Ha, 960 terms: 478 pass-1 launches with moments only,
-# 958 pass-2 launches with four accumulators; grouped steps included), GB300.  Per-launch traffic scales with the P_out blocks (the
+# 958 pass-2 launches with four accumulators; grouped steps included; atoms in
+# Hilbert order, as the 4-mu workloads run), GB300.  Per-launch traffic scales with the P_out blocks (the
 # operator has the same share of them).  Valid only for the kernel source it was
 # measured on: the sha256 of colstep.cu's text before its host-builder section
 # (the kernels and their launch code); after any change there the bench reports
 # traffic null.
 COL_KERNEL_END = "// Host: the column kernel's panels and work streams"
 COL_TRAFFIC = {"colstep_sha256": "154741e02d152208e90026c68cebafde56a0824781690b584981970ab666ee15",
-               "blocks_P_out": 1183812, "pass1_bytes": 465.4e6, "pass2_4acc_bytes": 867.9e6}
+               "blocks_P_out": 1183812, "pass1_bytes": 453.7e6, "pass2_4acc_bytes": 857.9e6, "order": "hilbert"}
 SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 
 WORKLOADS = {
     # The mixed-precision density matrix: 10,000 atoms x 4, 10 bohr cutoff,
     # 4 simultaneous mu (the bracket of a half-length moment pass).
+    # The atoms are relabelled along a Hilbert curve inside the solve (inputs and
+    # F stay in the generator's labelling).
     "foe_mixed_40k": dict(n_atoms=10000, r_c=10.0, r_buf=4.0, kT=0.005, N_e=20000.0, tol=1e-7, tol_S=1e-10,
-                          precision="f32", n_mu=4, form="mu4"),
+                          precision="f32", n_mu=4, form="mu4", order="hilbert"),
     # The same solve as moment pass + bisection + accumulation pass at mu*.
     "foe_mixed_40k_twopass": dict(n_atoms=10000, r_c=10.0, r_buf=4.0, kT=0.005, N_e=20000.0, tol=1e-7,
                                   tol_S=1e-10, precision="f32", n_mu=1, form="twopass"),
@@ -77,11 +80,11 @@ WORKLOADS = {
                                    tol_S=1e-10, precision="f32", n_mu=1, form="twopass"),
     # The same solve on 3,000 atoms (12,000 rows): profiling stand-in for the launch list.
     "foe_mixed_12k": dict(n_atoms=3000, r_c=10.0, r_buf=4.0, kT=0.005, N_e=6000.0, tol=1e-7, tol_S=1e-10,
-                          precision="f32", n_mu=4, form="mu4"),
+                          precision="f32", n_mu=4, form="mu4", order="hilbert"),
     # Same 12,000-row system at kT = 0.05 (about 10x fewer terms): keeps a per-launch
     # profiler capture of a whole solve short.
     "foe_mixed_12k_kT05": dict(n_atoms=3000, r_c=10.0, r_buf=4.0, kT=0.05, N_e=6000.0, tol=1e-7, tol_S=1e-10,
-                               precision="f32", n_mu=4, form="mu4"),
+                               precision="f32", n_mu=4, form="mu4", order="hilbert"),
     # The smearing chosen on the fly on the 12,000-row system: two-pass solves
     # from kT = 0.04 Ha, halved until E = Tr(K H) and E' of the same polynomials
     # at 1.25 kT differ by at most dE_tol (0.2 Ha, 6.7e-5 Ha per atom).
@@ -282,7 +285,7 @@ def run_cheb(args, rank: int, world: int, local: int):
     # per-geometry setup: patterns, plans, gather plans, S^-1/2 and G
     torch.cuda.synchronize()
     ts = time.time()
-    pb = solve.problem_from_system(sysm, cfg["r_buf"], dev, prec)
+    pb = solve.problem_from_system(sysm, cfg["r_buf"], dev, prec, order=cfg.get("order"))
     torch.cuda.synchronize()
     plans_s = time.time() - ts
     ov = solve.overlap_setup(pb, cfg["tol_S"])
@@ -365,15 +368,17 @@ def run_cheb(args, rank: int, world: int, local: int):
     h_tr = torch.empty(1, dtype=torch.float64).pin_memory()
     h2d = sysm.H.size * 8
     d2h = h_F.numel() * 8 + 8
+    d_H = torch.empty_like(pb.H.vals)  # the host H lands here, then moves to the solve's labelling
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record()
     for j in range(args.e2e_steps):
-        pb.H.vals.copy_(h_H[j], non_blocking=True)
+        d_H.copy_(h_H[j], non_blocking=True)
+        pb.set_H(d_H)
         o = solve_once()
-        h_F.copy_(o["F"], non_blocking=True)
+        h_F.copy_(pb.to_caller_out(o["F"]), non_blocking=True)
         h_tr.copy_(o["trace_FS"], non_blocking=True)
     f1.record()
     torch.cuda.synchronize()
@@ -409,7 +414,7 @@ def run_cheb(args, rank: int, world: int, local: int):
         gbs = alg_bytes / (avg_ms / 1e3) / 1e9
         alu_peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
         hbm_peak, hbm_src = measured_hbm_peak()
-        traffic = col_traffic_per_launch(form, cfg["n_mu"], launches_pass, nnz_out)
+        traffic = col_traffic_per_launch(form, cfg["n_mu"], launches_pass, nnz_out, order=cfg.get("order"))
         roof = {"bound": "alu", "achieved": round(tflops, 3), "peak": round(alu_peak, 3), "unit": "TFLOP/s",
                 "frac": round(tflops / alu_peak, 4), "traffic": traffic,
                 "peak_source": "FP32 FMA unit count: 152 SMs x 128 lanes x 2 flops x 2070 MHz",
@@ -445,6 +450,7 @@ def run_cheb(args, rank: int, world: int, local: int):
                    "setup_outside_timed_region": "patterns, plans, gather plans, S^-1/2, G (fixed overlap)",
                    "setup_s": round(setup_s, 2), "patterns_and_plans_s": round(plans_s, 2),
                    "parallelism": f"replicas x{world}",
+                   "atom_order": cfg.get("order") or "generator's (Morton)",
                    "l2": "inputs larger than L2 (no flush)"},
         "pass_ms": [round(x, 1) for x in p_ms],
         "roofline": roof,
@@ -721,11 +727,13 @@ def col_kernel_measured(text: str | None = None) -> bool:
     return hashlib.sha256(kernel.encode()).hexdigest() == COL_TRAFFIC["colstep_sha256"]
 
 
-def col_traffic_per_launch(form: str, n_mu: int, launches_pass, nnz_out: int, measured: bool | None = None):
+def col_traffic_per_launch(form: str, n_mu: int, launches_pass, nnz_out: int, measured: bool | None = None,
+                           order: str | None = None):
     """Measured DRAM bytes per k_colstep launch of a 4-mu solve, scaled to this
     system's P_out blocks and averaged over the solve's two passes; None for
-    other forms or when the kernel source differs from the measured one."""
-    if form != "mu4" or n_mu != 4 or len(launches_pass) != 2:
+    other forms, another atom order, or when the kernel source differs from
+    the measured one."""
+    if form != "mu4" or n_mu != 4 or len(launches_pass) != 2 or order != COL_TRAFFIC["order"]:
         return None
     if not (col_kernel_measured() if measured is None else measured):
         return None

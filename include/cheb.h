@@ -388,6 +388,40 @@ int cheb_transpose(const cheb_plan *plan, const double *A, double *out, void *st
 int cheb_block_diag(int32_t nsys, const cheb_bsr *parts, int64_t *out_row_ptr, int32_t *out_col_idx,
                     void *out_vals, int32_t elem_bytes, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Locality relabelling of a system (the paper has no counterpart: the column
+ * kernel takes panels of consecutive block columns, which column independence
+ * (Sec. "Expansion in Chebyshev polynomials") allows, and atoms that lie
+ * close together give panels with small unions of rows, so fewer operator
+ * entries per step).  A system is relabelled by building its patterns from the
+ * reordered atoms (cheb_pattern_build gives the relabelled patterns exactly)
+ * and moving values between the labellings.
+ *   locality_order: perm (device int64[n_atoms]) = the atoms in the order of a
+ *     3-D Hilbert curve through the periodic box of edge box (J. Skilling,
+ *     AIP Conf. Proc. 707, 381 (2004)): cell coordinates floor(1024 frac(x /
+ *     box)) per axis, key = the 30-bit Hilbert index, ties by atom index.
+ *     perm[i'] = the old index of new atom i'.  xyz: device double[n_atoms][3].
+ *     Workspace: cheb_locality_order_ws(n_atoms) bytes (8 per atom, rounded up
+ *     to a power of two).  Asynchronous.
+ *   position_map: map (device int64[P_new->nnzb]) = position in P_old of block
+ *     (perm[I'], perm[J']) for each block (I', J') of P_new (the same number
+ *     of rows and blocks).  Host-returning; CHEB_ERR_INVALID if a block is
+ *     missing or perm is not within [0, nbr).  Workspace: 4 bytes.
+ *   gather_rows: dst[i][c] = src[map[i]][c], i < n, c < width (device
+ *     doubles); rows whose map is outside [0, n_src) are written as 0.
+ *   scatter_rows: dst[map[i]][c] = src[i][c]; rows whose map is outside
+ *     [0, n_dst) are skipped.  Both asynchronous; src must not alias dst.
+ */
+size_t cheb_locality_order_ws(int64_t n_atoms);
+int cheb_locality_order(const double *xyz, int64_t n_atoms, double box, int64_t *perm, void *ws,
+                        size_t ws_bytes, void *stream);
+int cheb_position_map(const cheb_bsr *P_new, const cheb_bsr *P_old, const int64_t *perm, int64_t *map,
+                      void *ws, size_t ws_bytes, void *stream);
+int cheb_gather_rows(const double *src, int64_t n_src, const int64_t *map, int64_t n, int32_t width,
+                     double *dst, void *stream);
+int cheb_scatter_rows(const double *src, const int64_t *map, int64_t n, int32_t width, double *dst,
+                      int64_t n_dst, void *stream);
+
 /* Keep the blocks of A (FP64 on pattern PA) that lie in pattern P: out = device
  * double[P->nnzb*16]; blocks of P outside PA are written as zero.
  * Asynchronous. */

@@ -35,7 +35,8 @@ EXPORTS = [
     "cheb_masked_product", "cheb_transpose", "cheb_restrict", "cheb_trace_workspace_size", "cheb_trace",
     "cheb_penalty_trace", "cheb_mu_search", "cheb_mu_search_noalloc", "cheb_newton_schulz", "cheb_newton_schulz_isqrt",
     "cheb_plan_col_info", "cheb_penalty_check", "cheb_mu_nodes", "cheb_lagrange_weights", "cheb_bounds_spd",
-    "cheb_widen_bounds", "cheb_mlp_bracket",
+    "cheb_widen_bounds", "cheb_mlp_bracket", "cheb_locality_order_ws", "cheb_locality_order", "cheb_position_map",
+    "cheb_gather_rows", "cheb_scatter_rows",
     "cheb_series_value", "cheb_bounds_warm", "cheb_plan_set_gather_builder", "cheb_plan_lists_copy", "cheb_set_plan_builder",
     "cheb_ssf_export_size", "cheb_ssf_export", "cheb_ssf_import_pattern", "cheb_ssf_import_values",
 ]
@@ -99,6 +100,11 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True) -> ctypes.CDLL:
         "cheb_penalty_check": ([p, i32, dbl, dbl, P(dbl), P(i32), p, sz, p], i32),
         "cheb_mu_nodes": ([dbl, dbl, i32, P(dbl)], i32),
         "cheb_widen_bounds": ([P(dbl), i32, dbl], i32),
+        "cheb_locality_order_ws": ([i64], sz),
+        "cheb_locality_order": ([p, i64, dbl, p, p, sz, p], i32),
+        "cheb_position_map": ([P(CBsr), P(CBsr), p, p, p, sz, p], i32),
+        "cheb_gather_rows": ([p, i64, p, i64, i32, p, p], i32),
+        "cheb_scatter_rows": ([p, p, i64, i32, p, i64, p], i32),
         "cheb_mlp_bracket": ([P(ctypes.c_float), dbl, dbl, dbl, dbl, dbl, P(dbl), P(dbl)], i32),
         "cheb_series_value": ([p, p, i32, p, p], i32),
         "cheb_plan_set_gather_builder": ([p, i32], i32),
@@ -513,6 +519,46 @@ def masked_product(plan: Plan, L: Bsr, R: torch.Tensor, C: torch.Tensor, alpha: 
 def transpose(plan: Plan, A: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     out = torch.empty_like(A) if out is None else out
     _check(load().cheb_transpose(plan.handle, _ptr(A), _ptr(out), _stream(stream)))
+    return out
+
+
+def locality_order(xyz: torch.Tensor, box_L: float, stream=None) -> torch.Tensor:
+    """cheb_locality_order: device int64 permutation (new atom -> old atom) along a Hilbert curve."""
+    n = xyz.shape[0]
+    lib = load()
+    nb = int(lib.cheb_locality_order_ws(n))
+    ws = _ws(nb, xyz.device)
+    perm = torch.empty(n, dtype=torch.int64, device=xyz.device)
+    _check(lib.cheb_locality_order(_ptr(xyz), n, float(box_L), _ptr(perm), ctypes.c_void_p(_aligned(ws)), nb,
+                                   _stream(stream)))
+    return perm
+
+
+def position_map(P_new: Bsr, P_old: Bsr, perm: torch.Tensor, stream=None) -> torch.Tensor:
+    """cheb_position_map: device int64 position in P_old of every block of P_new."""
+    m = torch.empty(P_new.nnzb, dtype=torch.int64, device=perm.device)
+    ws = _ws(4, perm.device)
+    cn, co = P_new.c(), P_old.c()
+    _check(load().cheb_position_map(ctypes.byref(cn), ctypes.byref(co), _ptr(perm), _ptr(m),
+                                    ctypes.c_void_p(_aligned(ws)), 4, _stream(stream)))
+    return m
+
+
+def gather_rows(src: torch.Tensor, mapping: torch.Tensor, width: int, out: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """cheb_gather_rows: out row i = src row mapping[i] (rows of width doubles)."""
+    n = mapping.shape[0]
+    if out is None:
+        out = torch.empty(n * width, dtype=torch.float64, device=src.device)
+    _check(load().cheb_gather_rows(_ptr(src), src.numel() // width, _ptr(mapping), n, width, _ptr(out),
+                                   _stream(stream)))
+    return out
+
+
+def scatter_rows(src: torch.Tensor, mapping: torch.Tensor, width: int, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """cheb_scatter_rows: out row mapping[i] = src row i (rows of width doubles)."""
+    _check(load().cheb_scatter_rows(_ptr(src), _ptr(mapping), mapping.shape[0], width, _ptr(out),
+                                    out.numel() // width, _stream(stream)))
     return out
 
 

@@ -47,24 +47,62 @@ def _bsr_to_device(row_ptr, col_idx, vals, device) -> L.Bsr:
 
 
 class Problem:
-    """Device-resident inputs of one system: atoms, P_H with S and H, and P_out."""
+    """Device-resident inputs of one system: atoms, P_H with S and H, and P_out.
+
+    order="hilbert" relabels the atoms along a Hilbert curve (cheb_locality_order)
+    so that the column kernel's panels of consecutive columns hold atoms that lie
+    close together; the patterns, S, H and every result are then in the new
+    labelling, and set_H / to_caller_out move values from and to the caller's
+    labelling (the patterns built from the caller's atoms)."""
 
     def __init__(self, xyz: np.ndarray, L_box: float, r_c: float, r_buf: float, S_vals: np.ndarray,
-                 H_vals: np.ndarray, device, precision: int = L.F64, op_lists: bool = True):
+                 H_vals: np.ndarray, device, precision: int = L.F64, op_lists: bool = True,
+                 order: str | None = None):
         self.device = torch.device(device)
         self.L = float(L_box)
         self.r_c = float(r_c)
         self.r_out = float(r_c + r_buf)
-        self.xyz = torch.as_tensor(np.ascontiguousarray(xyz), dtype=torch.float64, device=self.device)
+        self.xyz_caller = torch.as_tensor(np.ascontiguousarray(xyz), dtype=torch.float64, device=self.device)
         self.S_host = S_vals
         self.H_host = H_vals
         self.precision = precision
         self.op_lists = op_lists
+        if order not in (None, "hilbert"):
+            raise ValueError(f"unknown order {order!r}")
+        self.perm = None
+        if order == "hilbert":
+            self.perm = L.locality_order(self.xyz_caller, self.L)
+            self.xyz = L.gather_rows(self.xyz_caller.reshape(-1), self.perm, 3).view(-1, 3)
+        else:
+            self.xyz = self.xyz_caller
         self.build_patterns()
-        self.S = self.P_H.with_vals(torch.as_tensor(np.ascontiguousarray(S_vals), dtype=torch.float64,
-                                                    device=self.device))
-        self.H = self.P_H.with_vals(torch.as_tensor(np.ascontiguousarray(H_vals), dtype=torch.float64,
-                                                    device=self.device))
+        S = torch.as_tensor(np.ascontiguousarray(S_vals), dtype=torch.float64, device=self.device)
+        H = torch.as_tensor(np.ascontiguousarray(H_vals), dtype=torch.float64, device=self.device)
+        if self.perm is not None:
+            rp, ci = L.pattern_build(self.xyz_caller, self.L, self.r_c)
+            self.P_H_caller = L.Bsr(rp, ci)
+            rp, ci = L.pattern_build(self.xyz_caller, self.L, self.r_out)
+            self.P_out_caller = L.Bsr(rp, ci)
+            self.map_H = L.position_map(self.P_H, self.P_H_caller, self.perm)
+            self.map_out = L.position_map(self.P_out, self.P_out_caller, self.perm)
+            S = L.gather_rows(S.reshape(-1), self.map_H, 16).view(S.shape)
+            H = L.gather_rows(H.reshape(-1), self.map_H, 16).view(H.shape)
+        self.S = self.P_H.with_vals(S)
+        self.H = self.P_H.with_vals(H)
+
+    def set_H(self, vals: torch.Tensor):
+        """New Hamiltonian values given in the caller's labelling (device, P_H order)."""
+        if self.perm is None:
+            self.H.vals.copy_(vals.view(self.H.vals.shape))
+        else:
+            L.gather_rows(vals.reshape(-1), self.map_H, 16, out=self.H.vals.view(-1))
+
+    def to_caller_out(self, F: torch.Tensor) -> torch.Tensor:
+        """Values on P_out (this problem's labelling) in the caller's labelling."""
+        if self.perm is None:
+            return F
+        out = torch.zeros_like(F)
+        return L.scatter_rows(F.reshape(-1), self.map_out, 16, out.view(-1)).view(F.shape)
 
     def build_patterns(self):
         rp, ci = L.pattern_build(self.xyz, self.L, self.r_c)
@@ -87,8 +125,9 @@ class Problem:
         return torch.zeros((self.P_out.nnzb, 4, 4), dtype=torch.float64, device=self.device)
 
 
-def problem_from_system(sysm, r_buf: float, device, precision: int = L.F64, op_lists: bool = True) -> Problem:
-    return Problem(sysm.xyz, sysm.L, sysm.r_cut, r_buf, sysm.S, sysm.H, device, precision, op_lists)
+def problem_from_system(sysm, r_buf: float, device, precision: int = L.F64, op_lists: bool = True,
+                        order: str | None = None) -> Problem:
+    return Problem(sysm.xyz, sysm.L, sysm.r_cut, r_buf, sysm.S, sysm.H, device, precision, op_lists, order)
 
 
 def powers(pb: Problem, exponents=(-1.0, 0.5, -0.5), tol: float = 1e-10, n_max: int = 512,
@@ -392,12 +431,13 @@ def selected_eigenvalues(pb: Problem, kT: float, intervals=(), levels=(), tol: f
 
 
 def foe_solve(sysm, r_buf: float, kT: float, N_e: float, tol: float = 1e-10, precision: int = L.F64,
-              device="cuda", **kw) -> dict:
-    """foe() on a synthetic system, with host copies of the main results."""
-    pb = problem_from_system(sysm, r_buf, device, precision)
+              device="cuda", order: str | None = None, **kw) -> dict:
+    """foe() on a synthetic system, with host copies of the main results (F_host
+    in the caller's labelling)."""
+    pb = problem_from_system(sysm, r_buf, device, precision, order=order)
     out = foe(pb, kT, N_e, tol=tol, **kw)
     torch.cuda.synchronize(pb.device)
     out["problem"] = pb
-    out["F_host"] = out["F"].cpu().numpy()
+    out["F_host"] = pb.to_caller_out(out["F"]).cpu().numpy()
     out["trace_FS"] = float(out["trace_FS"].item())
     return out

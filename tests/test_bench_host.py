@@ -76,9 +76,14 @@ def test_shipped_proposal_weights_match_the_network():
 
 
 def test_traffic_scales_with_blocks_and_is_tied_to_the_measured_source():
-    t = bench.col_traffic_per_launch("mu4", 4, [100, 200], bench.COL_TRAFFIC["blocks_P_out"] * 2, measured=True)
+    order = bench.COL_TRAFFIC["order"]
+    t = bench.col_traffic_per_launch("mu4", 4, [100, 200], bench.COL_TRAFFIC["blocks_P_out"] * 2, measured=True,
+                                     order=order)
     want = 2 * (bench.COL_TRAFFIC["pass1_bytes"] * 100 + bench.COL_TRAFFIC["pass2_4acc_bytes"] * 200) / 300
     assert t == int(want)
+    # measured in one atom order: another order's solve reports no figure
+    other = None if order == "hilbert" else "hilbert"
+    assert bench.col_traffic_per_launch("mu4", 4, [100, 200], 10, measured=True, order=other) is None
     assert bench.col_traffic_per_launch("twopass", 1, [100, 100], 10, measured=True) is None
     assert bench.col_traffic_per_launch("mu4", 4, [100, 200], 10, measured=False) is None
     # any change to the kernel text before the host section drops the figure

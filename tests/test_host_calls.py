@@ -45,3 +45,14 @@ def test_bracket_refuses_an_empty_interval():
         L.mlp_bracket([0.0, 0.0], 1.0, 1.0, 0.01, 0.05, 1.0)
     with pytest.raises(L.ChebError):
         L.mlp_bracket([0.0, 0.0], 0.0, 1.0, 0.01, 2.0, 1.0)
+
+
+def test_hilbert_reference_visits_face_adjacent_cells():
+    # the reference order used by the GPU test of cheb_locality_order: the first
+    # 16^3 indices of a Hilbert curve fill the corner cube, one face step apart
+    from hilbert_ref import hilbert_keys_ref
+    g = np.stack(np.meshgrid(*[np.arange(16)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    k = hilbert_keys_ref(g + 0.5, 1024.0)
+    o = np.argsort(k)
+    assert np.array_equal(k[o], np.arange(16 ** 3))
+    assert np.all(np.abs(np.diff(g[o], axis=0)).sum(axis=1) == 1)
